@@ -1,0 +1,540 @@
+#!/usr/bin/env python
+"""Throughput of the CPWL evaluation path on GB300.
+
+Workload (one "step", the whole path over one batch of synthetic input): the
+Gaussian exp(-x^2/2) on [-4, 4], the Lorentzian 1/(1+x^2) on [-10, 10] and
+J0 on [0, 50], each with N = 256, 1024 and 4096 intervals; for every
+(function, N): design of the nearly optimal partition (FP64 density, scan,
+inversion), vertex values of both pi_T and P_T (FP64), in-place rebuild of
+both tables, and evaluation of two query sets of 2^28 FP32 points each
+(uniform on the domain, seed 1; normal(0, 1.5) clipped to the domain,
+seed 2) through both tables.  Query sets are 1 GiB each (larger than L2), so
+no L2 flush is needed between launches.
+
+Metric: G PWL evaluations per second (whole job), next to the achieved HBM
+bandwidth of the evaluation kernel (8 bytes per query) against the measured
+copy bandwidth, the max error vs FP64 f, and fwd+bwd evaluations per second.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this build).  Under torchrun every rank runs
+the same workload on its own GPU (independent replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G PWL evals/s + HBM GB/s at stated max err vs FP64 f; fwd+bwd evals/s"
+FUNC_NAMES = ("gaussian", "lorentzian", "bessel_j0")
+NS = (256, 1024, 4096)
+FORMS = ("interp", "project")
+BYTES_FWD = 8   # 4 B of x in, 4 B of y out per query
+BYTES_BWD = 12  # x, gy in, gx out
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "eval_kernel_traffic.txt")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2m", type=int, default=28, help="queries per set (log2)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-log2", type=int, default=21, help="oracle queries per (table, set)")
+    ap.add_argument("--fwd-bwd-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (independent replicas; barrier + max over ranks)
+# ----------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power))}
+
+
+# ----------------------------------------------------------------------------
+# FP64 reference f for the error report (numpy / scipy, not the oracle)
+# ----------------------------------------------------------------------------
+def f64(name, x):
+    if name == "gaussian":
+        return np.exp(-0.5 * x * x)
+    if name == "lorentzian":
+        return 1.0 / (1.0 + x * x)
+    from scipy.special import j0
+    return j0(x)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the evaluation kernel from the last ncu
+    capture, or None if the kernel source changed since."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    vals = {}
+    for ln in open(TRAFFIC_FILE):
+        if "=" in ln and not ln.startswith("#"):
+            k, v = ln.split("=", 1)
+            vals[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_1510_02975_gb300", "csrc", "pwl_eval.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if vals.get("source_sha256_16") != h:
+        return None
+    try:
+        return float(vals["bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+class Workload:
+    def __init__(self, log2m: int):
+        import torch
+
+        import paper_1510_02975_gb300 as pwl
+        from paper_1510_02975_gb300 import workloads as W
+        self.torch, self.pwl, self.W = torch, pwl, W
+        self.m = 1 << log2m
+        self.funcs = [W.PAPER_FUNCTIONS[n] for n in FUNC_NAMES]
+        self.x = {}
+        for fi, f in enumerate(self.funcs):
+            self.x[(fi, "uniform")] = W.uniform_queries(f, self.m, seed=1)
+            self.x[(fi, "normal")] = W.normal_queries(f, self.m, seed=2)
+        self.y = torch.empty(self.m, dtype=torch.float32, device="cuda")
+        self.items = []  # (fi, N, knots, vi, vp, ws_d, ws_p, table_i, table_p)
+        lib = pwl._capi.load()
+        for fi, f in enumerate(self.funcs):
+            for N in NS:
+                kn = pwl.pwl_design(f, N)
+                vi = pwl.pwl_project(f, kn, "interp")
+                vp = pwl.pwl_project(f, kn, "project")
+                wsd = torch.empty(lib.pwl_design_workspace_size(N, 0), dtype=torch.uint8, device="cuda")
+                wsp = torch.empty(lib.pwl_project_workspace_size(N), dtype=torch.uint8, device="cuda")
+                ti = pwl.Table(kn, vi)
+                tp = pwl.Table(kn, vp)
+                self.items.append((fi, N, kn, vi, vp, wsd, wsp, ti, tp))
+        torch.cuda.synchronize()
+        self.evals_per_step = len(self.items) * len(FORMS) * 2 * self.m
+
+    def design_and_tables(self):
+        pwl = self.pwl
+        for fi, N, kn, vi, vp, wsd, wsp, ti, tp in self.items:
+            f = self.funcs[fi]
+            pwl.pwl_design(f, N, 0, "fp64", knots=kn, workspace=wsd)
+            pwl.pwl_project(f, kn, "interp", values=vi, workspace=wsp)
+            pwl.pwl_project(f, kn, "project", values=vp, workspace=wsp)
+            ti.update(kn, vi)
+            tp.update(kn, vp)
+
+    def step(self, events=None):
+        self.design_and_tables()
+        pwl = self.pwl
+        for fi, N, kn, vi, vp, wsd, wsp, ti, tp in self.items:
+            for t in (ti, tp):
+                for qs in ("uniform", "normal"):
+                    if events is not None:
+                        e0 = self.torch.cuda.Event(enable_timing=True)
+                        e1 = self.torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        pwl.pwl_eval(t.handle, self.x[(fi, qs)], self.y)
+                        e1.record()
+                        events.append((e0, e1))
+                    else:
+                        pwl.pwl_eval(t.handle, self.x[(fi, qs)], self.y)
+
+    def error_report(self, sample=1 << 20):
+        """max |y - f| (FP64 f) and max |y - v64| (FP64 PWL) on a sample of
+        each query set, per function and form, at N = 4096."""
+        torch = self.torch
+        out = {}
+        for fi, N, kn, vi, vp, wsd, wsp, ti, tp in self.items:
+            if N != NS[-1]:
+                continue
+            name = FUNC_NAMES[fi]
+            k64 = kn.cpu().numpy()
+            for form, t, v in (("interp", ti, vi), ("project", tp, vp)):
+                v64 = v.cpu().numpy()
+                ef, ep = 0.0, 0.0
+                for qs in ("uniform", "normal"):
+                    xs = self.x[(fi, qs)][:sample]
+                    y = self.pwl.pwl_eval(t.handle, xs).cpu().numpy().astype(np.float64)
+                    xd = xs.cpu().numpy().astype(np.float64)
+                    ef = max(ef, float(np.abs(y - f64(name, xd)).max()))
+                    ep = max(ep, float(np.abs(y - np.interp(xd, k64, v64)).max()))
+                out[f"{name}/{form}/N{N}"] = {"max_err_vs_f64_f": ef, "max_err_vs_f64_pwl": ep}
+        torch.cuda.synchronize()
+        return out
+
+
+def run_ours(args):
+    import torch
+    dist = Dist()
+    torch.cuda.set_device(dist.local)
+    dist.init("nccl")
+    from paper_1510_02975_gb300 import _build
+    _build.build()
+    wl = Workload(args.log2m)
+    for _ in range(max(args.warmup, 3)):
+        wl.step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    events = []
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        wl.step(events)
+    t1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    ms_max = dist.max(ms)
+    launch_ms = [a.elapsed_time(b) for a, b in events]
+    avg_launch_s = float(np.mean(launch_ms)) / 1e3
+    total_evals = wl.evals_per_step * args.steps * dist.world
+    value = total_evals / (ms_max / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_FWD * wl.m / avg_launch_s / 1e9
+
+    # time of the design / projection / table rebuild part of a step
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record()
+    for _ in range(3):
+        wl.design_and_tables()
+    d1.record()
+    torch.cuda.synchronize()
+    design_ms = d0.elapsed_time(d1) / 3
+
+    # fwd + bwd on the same tables and query sets
+    fb = fwd_bwd(wl, args.fwd_bwd_steps)
+    errors = wl.error_report()
+    e2e = None if args.no_e2e else run_e2e(wl, args.e2e_steps)
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample_log2)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "G evals/s",
+        "n_gpus": dist.world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: seeded uniform and clipped-normal FP32 queries; analytic functions",
+        "config": {
+            "workload": "3 functions (Gaussian [-4,4], Lorentzian [-10,10], J0 [0,50]) x N in {256,1024,4096} "
+                        "intervals x {pi_T, P_T}; per step FP64 design + projection + table rebuild, then "
+                        f"2 query sets of 2^{args.log2m} FP32 (uniform, normal(0,1.5) clipped) per table",
+            "evals_per_step": wl.evals_per_step,
+            "queries_per_set": wl.m,
+            "l2": "inputs larger than L2 (1 GiB per query set); no flush",
+            "parallelism": f"replicas x{dist.world}",
+        },
+        "roofline": {
+            "bound": "hbm",
+            "kernel": "eval_kernel<float>",
+            "achieved": round(achieved, 1),
+            "peak": peak,
+            "peak_kind": f"{peak_kind} copy bandwidth",
+            "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": recorded_traffic(),
+            "bytes_per_launch_algorithmic": BYTES_FWD * wl.m,
+            "avg_launch_ms": round(avg_launch_s * 1e3, 4),
+            "launches_timed": len(launch_ms),
+        },
+        "design_ms_per_step": round(design_ms, 3),
+        "fwd_bwd": fb,
+        "errors_N4096": errors,
+        "gpu_launches": gpu_launches_per_step(wl) * args.steps,
+        "clocks": clk,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+def gpu_launches_per_step(wl) -> int:
+    # per (function, N): design 5 (setup + 4), projections 1+1 (interp: setup + 1;
+    # project: setup + 2 -> counted 2 + 3), two table rebuilds of 2 kernels,
+    # four evaluations
+    per_item = 5 + 2 + 3 + 4 + 4
+    return per_item * len(wl.items)
+
+
+def fwd_bwd(wl, steps):
+    torch, pwl = wl.torch, wl.pwl
+    gy = wl.W.upstream_grad((wl.m,), seed=5)
+    gx = torch.empty_like(gy)
+    bufs = []
+    for fi, N, kn, vi, vp, wsd, wsp, ti, tp in wl.items:
+        for t in (ti, tp):
+            gv = torch.zeros(N + 1, device="cuda")
+            gk = torch.zeros(N + 1, device="cuda")
+            ws = torch.empty(pwl._capi.load().pwl_eval_backward_workspace_size(t.handle), dtype=torch.uint8,
+                             device="cuda")
+            bufs.append((fi, t, gv, gk, ws))
+
+    def one():
+        for fi, t, gv, gk, ws in bufs:
+            for qs in ("uniform", "normal"):
+                x = wl.x[(fi, qs)]
+                pwl.pwl_eval(t.handle, x, wl.y)
+                pwl.pwl_eval_backward(t.handle, x, gy, gx, gv, gk, ws)
+
+    one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    evals = len(bufs) * 2 * wl.m * steps
+    return {"value": round(evals / (ms / 1e3) / 1e9, 3), "unit": "G evals/s (forward + backward)",
+            "bytes_per_eval": BYTES_FWD + BYTES_BWD,
+            "gbs": round(evals * (BYTES_FWD + BYTES_BWD) / (ms / 1e3) / 1e9, 1)}
+
+
+def run_e2e(wl, steps):
+    """Same metric through the public API with host buffers: every step copies
+    its query sets from pinned host memory and reads every result back."""
+    torch, pwl = wl.torch, wl.pwl
+    hx = {k: v.cpu().pin_memory() for k, v in wl.x.items()}
+    hy = torch.empty(wl.m, dtype=torch.float32).pin_memory()
+    dx = {fi: torch.empty(wl.m, dtype=torch.float32, device="cuda") for fi in range(len(wl.funcs))}
+    dx2 = {fi: torch.empty(wl.m, dtype=torch.float32, device="cuda") for fi in range(len(wl.funcs))}
+
+    def one():
+        h2d = d2h = 0
+        wl.design_and_tables()
+        for fi in range(len(wl.funcs)):
+            dx[fi].copy_(hx[(fi, "uniform")], non_blocking=True)
+            dx2[fi].copy_(hx[(fi, "normal")], non_blocking=True)
+            h2d += 2 * wl.m * 4
+        for fi, N, kn, vi, vp, wsd, wsp, ti, tp in wl.items:
+            for t in (ti, tp):
+                for xs in (dx[fi], dx2[fi]):
+                    pwl.pwl_eval(t.handle, xs, wl.y)
+                    hy.copy_(wl.y, non_blocking=True)
+                    d2h += wl.m * 4
+        return h2d, d2h
+
+    one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h2d, d2h = one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": round(wl.evals_per_step * steps / (ms / 1e3) / 1e9, 3), "unit": "G evals/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_step(sample_log2: int, seed_offset: int = 0):
+    """One bounded sample of the workload on the FP64 CPU oracle: design and
+    both vertex-value forms for all 9 (function, N), then 2^sample_log2
+    queries of each set through each table.  Returns (evals, seconds)."""
+    import oracle
+    from paper_1510_02975_gb300 import workloads as W
+    rng = np.random.default_rng(1234 + seed_offset)
+    n = 1 << sample_log2
+    evals = 0
+    t0 = time.perf_counter()
+    for name in FUNC_NAMES:
+        f = W.PAPER_FUNCTIONS[name]
+        xu = rng.uniform(f["a"], f["b"], n).astype(np.float32).astype(np.float64)
+        xn = np.clip(rng.normal(0.0, 1.5, n), f["a"], f["b"]).astype(np.float32).astype(np.float64)
+        for N in NS:
+            k = oracle.design(f, N)
+            for form in FORMS:
+                v = oracle.values(f, k, form)
+                for xs in (xu, xn):
+                    oracle.evaluate(k, v, xs)
+                    evals += n
+    return evals, time.perf_counter() - t0
+
+
+def cpu_baseline(sample_log2: int):
+    import oracle
+    oracle.build()
+    evals, sec = oracle_step(sample_log2)
+    return {"value": round(evals / sec / 1e9, 6), "unit": "G evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 C oracle, one thread: design + pi_T + P_T for 3 functions x N in {list(NS)}, "
+                      f"then 2^{sample_log2} queries per (table, query set) = {evals} evaluations in {sec:.1f} s"}
+
+
+def run_reference(args):
+    dist = Dist()
+    if dist.rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sample = 18
+    for w in range(args.warmup):
+        oracle_step(sample, w)
+    total_e, total_s = 0, 0.0
+    for s in range(args.steps):
+        e, sec = oracle_step(sample, 100 + s)
+        total_e += e
+        total_s += sec
+    value = total_e / total_s / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 6), "unit": "G evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_s / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded uniform and clipped-normal queries; analytic functions",
+        "impl": "reference",
+        "config": {"workload": "3 functions x N in {256,1024,4096} x {pi_T, P_T}; design + values on the "
+                               f"oracle, then 2^{sample} queries per (table, query set) per step",
+                   "evals_per_step": total_e // max(args.steps, 1)},
+        "cpu_baseline": {"value": round(value, 6), "unit": "G evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"2^{sample} queries per (table, query set) per step"},
+        "e2e": {"value": round(value, 6), "unit": "G evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

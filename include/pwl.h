@@ -1,0 +1,235 @@
+/*
+ * pwl.h -- C ABI of libpwl, a single-GPU (GB300, sm_103a) library that
+ * evaluates a continuous function f at very many points through its nearly
+ * optimal continuous piecewise-linear (CPWL) approximation, following
+ * Berjon et al., "Optimal Piecewise Linear Function Approximation for
+ * GPU-based Applications" (IEEE Trans. Cybernetics, 2015).
+ *
+ * The calls follow the paper's statement of the problem (Section II-B): f is
+ * continuous on I = [a, b]; a partition T = {a = x_0 < ... < x_N = b} has N
+ * intervals and N+1 knots; a CPWL function v is given by its nodal values
+ * v(x_0..x_N) (Eq. 2); Algorithm 1 evaluates v at a point x*.
+ *
+ * Conventions shared by every call:
+ *   - Pointers named d_* (and every array argument unless marked "host") are
+ *     device pointers owned by the caller.  The library owns only the opaque
+ *     handles it returns (pwl_table, pwl_batch, pwl_channels), freed by the
+ *     matching *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it and return without waiting, except
+ *     where a call says "synchronizes".
+ *   - Every call returns a pwl_status.  Arguments are validated on the host
+ *     before anything is launched; on failure nothing is enqueued and
+ *     pwl_last_error() describes the problem (thread-local string).
+ *     PWL_ECUDA reports a CUDA launch or runtime error.
+ *   - Workspace arguments: scratch device memory of at least the size the
+ *     matching *_workspace_size call returns, 256-byte aligned, not used by
+ *     another call that runs at the same time.
+ *   - Sizes: 1 <= N <= 1048575 intervals per function; m >= 0 queries
+ *     (m == 0 is a no-op).
+ */
+#ifndef PWL_H
+#define PWL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PWL_OK = 0,
+    PWL_EINVAL = 1,   /* bad argument (size, pointer, non-increasing knots, ...) */
+    PWL_ENOMEM = 2,   /* device or host allocation failed                         */
+    PWL_ECUDA = 3,    /* CUDA runtime / launch error                             */
+    PWL_ENOTSUP = 4,  /* combination not supported                               */
+    PWL_ETIMEOUT = 5  /* a bounded device loop hit its iteration cap             */
+} pwl_status;
+
+/* Analytic functions f on [a, b] with their second derivative in closed form
+ * (the design step needs f'').  Parameters p[]:
+ *   PWL_F_GAUSSIAN   A exp(-(x - mu)^2 / (2 s^2))     p = {A, mu, s}     (Section V-A)
+ *   PWL_F_LORENTZIAN A / (1 + ((x - x0) / g)^2)        p = {A, x0, g}     (Eq. 25 with
+ *                    A = 1/(pi g) gives the paper's normalised form, Section V-B)
+ *   PWL_F_BESSEL_J0  A J0(alpha x)                     p = {A, alpha}     (Section V-C)
+ *   PWL_F_POLY       sum_{k=0..7} p[k] x^k                               (Fig. 1's quintic)
+ *   PWL_F_EXP        A exp(lambda x)                   p = {A, lambda}                    */
+typedef enum {
+    PWL_F_GAUSSIAN = 0,
+    PWL_F_LORENTZIAN = 1,
+    PWL_F_BESSEL_J0 = 2,
+    PWL_F_POLY = 3,
+    PWL_F_EXP = 4
+} pwl_kind;
+
+typedef struct {
+    int32_t kind;     /* pwl_kind */
+    int32_t reserved; /* must be 0 */
+    double a, b;      /* the interval I = [a, b], a < b, both finite */
+    double p[8];      /* parameters, see pwl_kind */
+} pwl_func;
+
+/* Which CPWL approximation of f the vertex values define (Section II-B). */
+typedef enum {
+    PWL_INTERP = 0,  /* linear interpolant pi_T f: v_i = f(x_i)            (Eq. 3)    */
+    PWL_PROJECT = 1  /* L2 orthogonal projection P_T f: M c = b, v_i = c_i  (Eqs. 4-6) */
+} pwl_form;
+
+/* Storage type of a vertex-value table or of a query / result stream.  The
+ * interpolation arithmetic is FP32 in every case. */
+typedef enum { PWL_FP32 = 0, PWL_BF16 = 1, PWL_FP16 = 2 } pwl_dtype;
+
+/* Precision of the integrands of the design and projection steps (the
+ * density |f''|^{2/5} and f at quadrature nodes).  Prefix sums, knot
+ * inversion, quadrature sums and the tridiagonal solve are FP64 in both. */
+typedef enum { PWL_PREC_FP64 = 0, PWL_PREC_FP32 = 1 } pwl_precision;
+
+typedef struct pwl_table_s* pwl_table;
+typedef struct pwl_batch_s* pwl_batch;
+typedef struct pwl_channels_s* pwl_channels;
+
+/* ------------------------------------------------------------------------ */
+/* Library                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Thread-local description of the last failure of a call on this thread. */
+const char* pwl_last_error(void);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int32_t pwl_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Design: knots of the nearly optimal partition T* (Section III-B)          */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of workspace pwl_design needs for n_intervals and m_cells. */
+size_t pwl_design_workspace_size(int64_t n_intervals, int64_t m_cells);
+
+/* Knots x_0..x_N of T* for f (Eqs. 16-18): the local knot density
+ * |f''|^{2/5} is sampled at the midpoints t_k = a + (k + 1/2)(b - a)/M of M
+ * uniform cells (precision per `precision`), prefix-summed in FP64 into
+ * G_k = delta * sum_{j<k} d_j (the numerator of Eq. 18 by the midpoint rule),
+ * and inverted: x_0 = a, x_N = b, and for 0 < i < N, with tau_i = i G_M / N,
+ * the cell is the largest k with G_k <= tau_i and d_k > 0 and
+ * x_i = a + k delta + (tau_i - G_k) / d_k.  If G_M == 0 (f linear on I) the
+ * uniform partition is returned.
+ *   f          host pointer to the function descriptor
+ *   n_intervals N >= 1
+ *   m_cells    M >= 1 density cells; 0 selects 64 N
+ *   precision  pwl_precision of the density samples
+ *   d_knots    device, N+1 doubles (output, strictly increasing)
+ * Errors: PWL_EINVAL for a bad descriptor, sizes or workspace.             */
+pwl_status pwl_design(const pwl_func* f, int64_t n_intervals, int64_t m_cells, int32_t precision,
+                      double* d_knots, void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Vertex values (Section II-B)                                              */
+/* ------------------------------------------------------------------------ */
+
+size_t pwl_project_workspace_size(int64_t n_intervals);
+
+/* Vertex values of pi_T f (form PWL_INTERP, v_i = f(x_i), Eq. 3) or of
+ * P_T f (form PWL_PROJECT, Eqs. 4-6): b_i = <f, phi_i> by quad_points-point
+ * Gauss-Legendre quadrature on every interval (1 <= quad_points <= 16; 0
+ * selects 8), the tridiagonal Gram matrix M_ii = (h_i + h_{i+1})/3,
+ * M_{i,i+1} = h_{i+1}/6, and M c = b solved in FP64 by cyclic reduction.
+ *   d_knots   device, N+1 strictly increasing doubles (e.g. from pwl_design)
+ *   d_values  device, N+1 doubles (output)
+ * The workspace (pwl_project_workspace_size bytes) also carries the function
+ * descriptor to the device, so it is needed for both forms.                */
+pwl_status pwl_project(const pwl_func* f, const double* d_knots, int64_t n_intervals,
+                       int32_t form, int32_t quad_points, int32_t precision, double* d_values,
+                       void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Device representation of a CPWL function (inputs of Algorithm 1)          */
+/* ------------------------------------------------------------------------ */
+
+/* Builds a table from FP64 knots and values (device arrays of N+1).  Knots
+ * are rounded to FP32 and values to `value_dtype` (round to nearest); the
+ * table evaluates exactly that CPWL function.  For evaluation it adds a
+ * uniform cell index over [x_0, x_N]: k_cells cells (0 = automatic), each
+ * holding the knot at or before it with the slopes on both sides, so that
+ * Algorithm 1's search step is one lookup.
+ * Synchronizes `stream` (it validates the rounded knots and sizes the
+ * index).  Errors: PWL_EINVAL if the rounded knots are not strictly
+ * increasing or a value or slope is not finite.                            */
+pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_t n_intervals,
+                           int32_t value_dtype, int64_t k_cells, pwl_table* out, void* stream);
+
+/* Rebuilds the table in place from new FP64 knots and values (same N, value
+ * dtype and cell count), asynchronously on `stream` and without allocating:
+ * the call a training or design loop makes every step.  The knots must stay
+ * strictly increasing after rounding to FP32 and every value and slope
+ * finite; this call does not check (pwl_table_check does).  It must not
+ * overlap other work on the same table.                                     */
+pwl_status pwl_table_update(pwl_table t, const double* d_knots, const double* d_values, void* stream);
+
+/* Status of the last build or update: PWL_EINVAL if the rounded knots were
+ * not strictly increasing or a value or slope not finite.  Synchronizes
+ * `stream`.                                                                 */
+pwl_status pwl_table_check(pwl_table t, void* stream);
+
+pwl_status pwl_table_destroy(pwl_table t);
+
+typedef struct {
+    int64_t n_intervals;   /* N */
+    int64_t k_cells;       /* cells of the uniform index */
+    int64_t n_chain;       /* extra records for cells holding more than one knot */
+    int32_t value_dtype;   /* pwl_dtype of the stored values */
+    int32_t reserved;
+    float a, b;            /* x_0, x_N as stored (FP32) */
+    const float* d_knots;  /* device, N+1 FP32 knots used by every kernel */
+    const void* d_values;  /* device, N+1 values in value_dtype */
+    size_t eval_smem_bytes;     /* shared memory one forward CTA stages */
+    size_t backward_smem_bytes; /* shared memory one backward CTA stages */
+} pwl_table_info;
+
+pwl_status pwl_table_get_info(pwl_table t, pwl_table_info* info);
+
+/* ------------------------------------------------------------------------ */
+/* Evaluation (Algorithm 1)                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* y[q] = v(x[q]) for q < m (Algorithm 1), the interpolation in FP32.  x and
+ * y are device arrays of m elements of io_dtype (PWL_FP32, PWL_BF16 or
+ * PWL_FP16; the same for both).  x outside [x_0, x_N] is clamped (y = v_0 or
+ * v_N); x = x_N uses the last interval; NaN gives NaN.  Any alignment; the
+ * 16-byte vector path is used when x and y share their alignment.  x and y
+ * may be the same array.                                                   */
+pwl_status pwl_eval(pwl_table t, const void* d_x, void* d_y, int64_t m, int32_t io_dtype,
+                    void* stream);
+
+/* Comparison paths for the measurements of Section V-A (Table I):
+ *   mode 0: Algorithm 1 with the binary search of Section IV on the FP32
+ *           knot table in shared memory (O(log N) per query);
+ *   mode 1: the same interval search as pwl_eval, then the texture unit's
+ *           linear filter at coordinate i - 1 + delta + 1/2 over the values
+ *           (Section IV-B); the filter weight is fixed point (8 fractional
+ *           bits), so results differ from pwl_eval by up to |v_i - v_{i-1}|/256.
+ * x, y: device FP32 arrays of m elements.                                  */
+pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* d_y, int64_t m,
+                            void* stream);
+
+/* Backward of pwl_eval for upstream gradients gy (FP32, m elements):
+ *   gx[q] = gy[q] * s_i (s_i the slope of x[q]'s interval; 0 if clamped)
+ *   g_values[j] += sum over queries of gy * dy/dv_j  (N+1 FP32, or NULL)
+ *   g_knots[j]  += sum over queries of gy * dy/dx_j  (N+1 FP32, or NULL)
+ * with dy/dv_{i-1} = 1 - delta, dy/dv_i = delta, dy/dx_{i-1} = -s (1 - delta),
+ * dy/dx_i = -s delta; a clamped query adds gy to g_values[0] or [N] only.
+ * g_values / g_knots are accumulated into (the caller zeroes them).  Each
+ * CTA accumulates with FP32 shared-memory atomics; the CTA partial sums are
+ * then reduced in a fixed order in FP64, so run-to-run differences stay at
+ * the FP32 rounding level of the in-CTA sums.  gx may alias gy.
+ * Workspace: pwl_eval_backward_workspace_size(t) bytes.                    */
+size_t pwl_eval_backward_workspace_size(pwl_table t);
+pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, float* d_gx,
+                             float* d_g_values, float* d_g_knots, int64_t m, void* d_workspace,
+                             size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PWL_H */

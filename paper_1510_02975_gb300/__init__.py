@@ -1,0 +1,252 @@
+"""GB300-native evaluation of nearly optimal continuous piecewise-linear
+(CPWL) approximations (Berjon et al., "Optimal Piecewise Linear Function
+Approximation for GPU-based Applications").
+
+Thin binding over the C ABI of libpwl.so (include/pwl.h).  The functions
+named like the C entry points take torch CUDA tensors, pass their pointers
+and the current stream, and raise PwlError on a non-zero status.  PyTorch is
+used only for device memory and streams; every step runs in the library's
+CUDA kernels.  There is no CPU fallback: without a built library or a GPU
+these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from ._capi import DTYPES, FORMS, KINDS, PRECISIONS, PwlError, PwlTableInfo, check, load, make_func
+
+__all__ = [
+    "PwlError", "pwl_design", "pwl_project", "pwl_table_build", "pwl_table_update", "pwl_table_check", "pwl_table_destroy", "pwl_table_get_info",
+    "pwl_eval", "pwl_eval_variant", "pwl_eval_backward", "Table", "design", "project", "PWLFunction",
+    "KINDS", "FORMS", "DTYPES", "PRECISIONS",
+]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _require(t, dtype, name, numel=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype} (got {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements (got {t.numel()})")
+
+
+def _workspace(nbytes: int, device):
+    torch = _torch()
+    # 256-byte aligned: the caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------------------
+# C entry points, same names
+# ----------------------------------------------------------------------------
+def pwl_design(f, n_intervals: int, m_cells: int = 0, precision: str = "fp64", knots=None,
+               workspace=None, stream=None):
+    """Knots of the nearly optimal partition (Section III-B) -> float64 (N+1,)."""
+    torch = _torch()
+    lib = load()
+    if knots is None:
+        knots = torch.empty(n_intervals + 1, dtype=torch.float64, device="cuda")
+    _require(knots, torch.float64, "knots", n_intervals + 1)
+    ws_n = lib.pwl_design_workspace_size(n_intervals, m_cells)
+    ws = workspace if workspace is not None and workspace.numel() >= ws_n else _workspace(ws_n, knots.device)
+    F = make_func(f)
+    check(lib.pwl_design(ctypes.byref(F), n_intervals, m_cells, PRECISIONS[precision], _ptr(knots),
+                         _ptr(ws), ws.numel(), _stream(stream)), "pwl_design")
+    return knots
+
+
+def pwl_project(f, knots, form: str = "project", quad_points: int = 8, precision: str = "fp64",
+                values=None, workspace=None, stream=None):
+    """Vertex values of pi_T f ("interp") or P_T f ("project") -> float64 (N+1,)."""
+    torch = _torch()
+    lib = load()
+    _require(knots, torch.float64, "knots")
+    n = knots.numel() - 1
+    if values is None:
+        values = torch.empty_like(knots)
+    _require(values, torch.float64, "values", n + 1)
+    ws_n = lib.pwl_project_workspace_size(n)
+    ws = workspace if workspace is not None and workspace.numel() >= ws_n else _workspace(ws_n, knots.device)
+    F = make_func(f)
+    check(lib.pwl_project(ctypes.byref(F), _ptr(knots), n, FORMS[form], quad_points, PRECISIONS[precision],
+                          _ptr(values), _ptr(ws), ws.numel(), _stream(stream)), "pwl_project")
+    return values
+
+
+def pwl_table_build(knots, values, value_dtype: str = "fp32", k_cells: int = 0, stream=None):
+    """Opaque table handle (int) for FP64 knots and values (synchronizes)."""
+    torch = _torch()
+    lib = load()
+    _require(knots, torch.float64, "knots")
+    _require(values, torch.float64, "values", knots.numel())
+    out = ctypes.c_void_p()
+    check(lib.pwl_table_build(_ptr(knots), _ptr(values), knots.numel() - 1, DTYPES[value_dtype], k_cells,
+                              ctypes.byref(out), _stream(stream)), "pwl_table_build")
+    return out.value
+
+
+def pwl_table_update(handle, knots, values, stream=None) -> None:
+    """Asynchronous in-place rebuild from new FP64 knots / values (same N)."""
+    torch = _torch()
+    _require(knots, torch.float64, "knots")
+    _require(values, torch.float64, "values", knots.numel())
+    check(load().pwl_table_update(ctypes.c_void_p(handle), _ptr(knots), _ptr(values), _stream(stream)),
+          "pwl_table_update")
+
+
+def pwl_table_check(handle, stream=None) -> None:
+    check(load().pwl_table_check(ctypes.c_void_p(handle), _stream(stream)), "pwl_table_check")
+
+
+def pwl_table_destroy(handle) -> None:
+    if handle:
+        check(load().pwl_table_destroy(ctypes.c_void_p(handle)), "pwl_table_destroy")
+
+
+def pwl_table_get_info(handle) -> dict:
+    info = PwlTableInfo()
+    check(load().pwl_table_get_info(ctypes.c_void_p(handle), ctypes.byref(info)), "pwl_table_get_info")
+    return {k: getattr(info, k) for k, _ in PwlTableInfo._fields_}
+
+
+def _io_dtype(t):
+    torch = _torch()
+    return {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}[t.dtype]
+
+
+def pwl_eval(handle, x, y=None, stream=None):
+    """y = v(x) (Algorithm 1); x, y float32 / bfloat16 / float16 CUDA tensors."""
+    torch = _torch()
+    if y is None:
+        y = torch.empty_like(x)
+    if x.dtype != y.dtype or x.numel() != y.numel():
+        raise ValueError("x and y must have the same dtype and size")
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("x and y must be contiguous CUDA tensors")
+    check(load().pwl_eval(ctypes.c_void_p(handle), _ptr(x), _ptr(y), x.numel(), _io_dtype(x), _stream(stream)),
+          "pwl_eval")
+    return y
+
+
+def pwl_eval_variant(handle, mode: int, x, y=None, stream=None):
+    """Comparison paths: mode 0 binary search (Algorithm 1), mode 1 texture filter."""
+    torch = _torch()
+    _require(x, torch.float32, "x")
+    if y is None:
+        y = torch.empty_like(x)
+    _require(y, torch.float32, "y", x.numel())
+    check(load().pwl_eval_variant(ctypes.c_void_p(handle), mode, _ptr(x), _ptr(y), x.numel(), _stream(stream)),
+          "pwl_eval_variant")
+    return y
+
+
+def pwl_eval_backward(handle, x, gy, gx=None, g_values=None, g_knots=None, workspace=None, stream=None):
+    """Backward of pwl_eval: returns gx; accumulates into g_values / g_knots."""
+    torch = _torch()
+    lib = load()
+    _require(x, torch.float32, "x")
+    _require(gy, torch.float32, "gy", x.numel())
+    if gx is None:
+        gx = torch.empty_like(x)
+    _require(gx, torch.float32, "gx", x.numel())
+    for name, t in (("g_values", g_values), ("g_knots", g_knots)):
+        if t is not None:
+            _require(t, torch.float32, name)
+    need = lib.pwl_eval_backward_workspace_size(ctypes.c_void_p(handle))
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, x.device)
+    check(lib.pwl_eval_backward(ctypes.c_void_p(handle), _ptr(x), _ptr(gy), _ptr(gx), _ptr(g_values),
+                                _ptr(g_knots), x.numel(), _ptr(workspace), workspace.numel(), _stream(stream)),
+          "pwl_eval_backward")
+    return gx
+
+
+# ----------------------------------------------------------------------------
+# convenience layer
+# ----------------------------------------------------------------------------
+def design(f, n_intervals: int, m_cells: int = 0, precision: str = "fp64"):
+    return pwl_design(f, n_intervals, m_cells, precision)
+
+
+def project(f, knots, form: str = "project", quad_points: int = 8, precision: str = "fp64"):
+    return pwl_project(f, knots, form, quad_points, precision)
+
+
+class Table:
+    """A CPWL function on the GPU (owns a pwl_table)."""
+
+    def __init__(self, knots, values, value_dtype: str = "fp32", k_cells: int = 0):
+        self.handle = pwl_table_build(knots, values, value_dtype, k_cells)
+        self.info = pwl_table_get_info(self.handle)
+        self.n_intervals = int(self.info["n_intervals"])
+
+    def __call__(self, x, out=None):
+        return pwl_eval(self.handle, x, out)
+
+    def eval(self, x, out=None):
+        return pwl_eval(self.handle, x, out)
+
+    def variant(self, mode: int, x, out=None):
+        return pwl_eval_variant(self.handle, mode, x, out)
+
+    def update(self, knots, values):
+        pwl_table_update(self.handle, knots, values)
+
+    def backward(self, x, gy, gx=None, g_values=None, g_knots=None):
+        return pwl_eval_backward(self.handle, x, gy, gx, g_values, g_knots)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pwl_table_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PWLFunction:
+    """torch.autograd.Function over a Table: y = v(x), with gradients w.r.t.
+    x (and the table's values / knots through table_grads)."""
+
+    @staticmethod
+    def apply(table: Table, x, table_grads=None):
+        torch = _torch()
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, xx):
+                ctx.save_for_backward(xx)
+                return pwl_eval(table.handle, xx.contiguous())
+
+            @staticmethod
+            def backward(ctx, gy):
+                (xx,) = ctx.saved_tensors
+                gv = gk = None
+                if table_grads is not None:
+                    gv, gk = table_grads
+                gx = pwl_eval_backward(table.handle, xx.contiguous(), gy.contiguous(), None, gv, gk)
+                return gx
+
+        return _F.apply(x)

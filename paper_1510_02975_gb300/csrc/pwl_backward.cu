@@ -1,0 +1,264 @@
+// pwl_backward.cu -- gradients of Algorithm 1 w.r.t. the query x, the
+// vertex values v_j and the knots x_j.
+//
+// With interval i of x, h = x_i - x_{i-1}, delta = (x - x_{i-1})/h and slope s:
+//   dy/dx = s,  dy/dv_{i-1} = 1 - delta,  dy/dv_i = delta,
+//   dy/dx_{i-1} = -s (1 - delta),  dy/dx_i = -s delta.
+// Because s is constant on an interval, the table gradients only need two
+// sums per interval, A_i = sum gy (1 - delta) and B_i = sum gy delta:
+//   g_v[j]  += A_{j+1} + B_j            g_x[j] += -s_{j+1} A_{j+1} - s_j B_j
+// (clamped queries add gy to g_v[0] or g_v[N] only).
+//
+// Pass 1 (persistent grid): every CTA stages the backward records and the
+// reciprocal lengths, streams (x, gy) -> gx with 16-byte vectors, and
+// accumulates A, B in shared memory with FP32 atomics; it then writes its
+// partial sums to the workspace (one row per CTA).
+// Pass 2: one thread per knot sums the CTA rows in a fixed order (FP64) and
+// forms g_v and g_x (the order of the in-CTA atomics still varies from run
+// to run, so the sums are reproducible to FP32 rounding, not bit for bit).
+#include <math.h>
+
+#include <algorithm>
+
+#include "pwl_backward.cuh"
+
+namespace pwl {
+
+namespace {
+
+constexpr int kBwdUnroll = 2;
+
+// Accumulator layout per CTA row (FP32, 2 (N + 2) entries):
+//   A[0]      gy of queries clamped on the left  -> g_v[0]
+//   A[1..N]   sum gy (1 - delta) on interval i
+//   A[N+1]    gy of queries clamped on the right -> g_v[N]
+//   B[0..N+1] sum gy delta on interval i (entries 0 and N+1 unused)
+struct BwdArgs {
+    const float4* rec;  // backward records {x_j, j, s_j, s_{j+1} | link}
+    const TableHeader* hdr;
+    const float* inv_h;
+    int N, K, n_smem, max_chain;
+    float a, b, inv_w, off;
+    int64_t nvec;       // float4 vectors (x, gy and gx all 16-byte aligned), else 0
+};
+
+template <bool CHAINS>
+__device__ __forceinline__ float bwd_one(float x, float g, const float4* __restrict__ srec,
+                                         const float* __restrict__ s_ih, float* accA, float* accB,
+                                         const BwdArgs& p)
+{
+    if (x != x) return x;  // NaN: no table contribution
+    if (x < p.a) {
+        atomicAdd(accA, g);
+        return 0.0f;
+    }
+    if (x > p.b) {
+        atomicAdd(accA + p.N + 1, g);
+        return 0.0f;
+    }
+    const int c = cell_of(x, p.inv_w, p.off, p.K);
+    float4 r = (c < p.n_smem) ? srec[c] : __ldg(p.rec + c);
+    if (CHAINS) {
+        for (int it = 0; it < p.max_chain && x >= r.x && is_link(r.w); ++it) {
+            const int j = link_index(r.w);
+            r = (j < p.n_smem) ? srec[j] : __ldg(p.rec + j);
+        }
+    }
+    const int j = __float_as_int(r.y);
+    int i;
+    float s, one_minus, delta;
+    if (x < r.x) {  // interval j, measured from its right end
+        i = j;
+        s = r.z;
+        one_minus = (r.x - x) * s_ih[j];
+        delta = 1.0f - one_minus;
+    } else if (j < p.N) {  // interval j + 1
+        i = j + 1;
+        s = r.w;
+        delta = (x - r.x) * s_ih[j + 1];
+        one_minus = 1.0f - delta;
+    } else {  // x == x_N: interval N with delta = 1
+        i = p.N;
+        s = r.z;
+        delta = 1.0f;
+        one_minus = 0.0f;
+    }
+    atomicAdd(accA + i, g * one_minus);
+    atomicAdd(accB + i, g * delta);
+    return g * s;
+}
+
+template <bool CHAINS>
+__device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __restrict__ srec,
+                                              const float* __restrict__ s_ih, float* accA, float* accB,
+                                              const float* x, const float* gy, float* gx, int64_t m)
+{
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float4* xv = reinterpret_cast<const float4*>(x);
+    const float4* gv = reinterpret_cast<const float4*>(gy);
+    float4* ov = reinterpret_cast<float4*>(gx);
+    int64_t i = tid;
+    for (; i + (kBwdUnroll - 1) * nthr < p.nvec; i += kBwdUnroll * nthr) {
+        float4 xs[kBwdUnroll], gs[kBwdUnroll];
+#pragma unroll
+        for (int u = 0; u < kBwdUnroll; ++u) {
+            xs[u] = __ldcs(xv + i + u * nthr);
+            gs[u] = __ldcs(gv + i + u * nthr);
+        }
+#pragma unroll
+        for (int u = 0; u < kBwdUnroll; ++u) {
+            float4 o;
+            o.x = bwd_one<CHAINS>(xs[u].x, gs[u].x, srec, s_ih, accA, accB, p);
+            o.y = bwd_one<CHAINS>(xs[u].y, gs[u].y, srec, s_ih, accA, accB, p);
+            o.z = bwd_one<CHAINS>(xs[u].z, gs[u].z, srec, s_ih, accA, accB, p);
+            o.w = bwd_one<CHAINS>(xs[u].w, gs[u].w, srec, s_ih, accA, accB, p);
+            __stcs(ov + i + u * nthr, o);
+        }
+    }
+    for (; i < p.nvec; i += nthr) {
+        const float4 xs = __ldcs(xv + i), gs = __ldcs(gv + i);
+        float4 o;
+        o.x = bwd_one<CHAINS>(xs.x, gs.x, srec, s_ih, accA, accB, p);
+        o.y = bwd_one<CHAINS>(xs.y, gs.y, srec, s_ih, accA, accB, p);
+        o.z = bwd_one<CHAINS>(xs.z, gs.z, srec, s_ih, accA, accB, p);
+        o.w = bwd_one<CHAINS>(xs.w, gs.w, srec, s_ih, accA, accB, p);
+        __stcs(ov + i, o);
+    }
+    for (int64_t q = p.nvec * 4 + tid; q < m; q += nthr)
+        gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, p);
+}
+
+__global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, const float* x, const float* gy,
+                                                        float* gx, int64_t m, float* partials)
+{
+    extern __shared__ float4 s_dyn[];
+    float4* srec = s_dyn;
+    float* s_ih = reinterpret_cast<float*>(s_dyn + args.n_smem);
+    float* accA = s_ih + (args.N + 2);
+    float* accB = accA + (args.N + 2);
+    BwdArgs p = args;
+    const int n_chain = p.hdr->n_chain;
+    p.max_chain = p.hdr->max_chain;
+    p.n_smem = min(p.K + n_chain, p.n_smem);
+    for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) srec[i] = __ldg(p.rec + i);
+    for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) {
+        s_ih[i] = p.inv_h[i];
+        accA[i] = 0.0f;
+        accB[i] = 0.0f;
+    }
+    __syncthreads();
+    if (n_chain == 0)
+        backward_body<false>(p, srec, s_ih, accA, accB, x, gy, gx, m);
+    else
+        backward_body<true>(p, srec, s_ih, accA, accB, x, gy, gx, m);
+    __syncthreads();
+    float* row = partials + (size_t)blockIdx.x * 2 * (p.N + 2);
+    for (int k = threadIdx.x; k < 2 * (p.N + 2); k += blockDim.x) row[k] = accA[k];
+}
+
+// g_v[j] += A_{j+1} + B_j (+ clamped terms), g_x[j] += -s_{j+1} A_{j+1} - s_j B_j
+__global__ void backward_reduce_kernel(const float* __restrict__ partials, int rows, int N,
+                                       const float* __restrict__ slope, float* g_values, float* g_knots)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > N) return;
+    const int W = 2 * (N + 2);
+    double Aj1 = 0.0, Bj = 0.0, clamped = 0.0;
+    for (int r = 0; r < rows; ++r) {
+        const float* row = partials + (size_t)r * W;
+        if (j < N) Aj1 += (double)row[j + 1];
+        if (j > 0) Bj += (double)row[N + 2 + j];
+        if (j == 0) clamped += (double)row[0];
+        if (j == N) clamped += (double)row[N + 1];
+    }
+    if (g_values) g_values[j] += (float)(Aj1 + Bj + clamped);
+    if (g_knots) {
+        const double gk = -(double)slope[j + 1] * Aj1 - (double)slope[j] * Bj;
+        g_knots[j] += (float)gk;
+    }
+}
+
+}  // namespace
+
+BwdShape backward_shape(pwl_table t)
+{
+    BwdShape s{};
+    s.n_smem = backward_smem_records(t);
+    if (s.n_smem < 0) return s;
+    s.smem = backward_smem_bytes(t);
+    s.threads = 1024;
+    if (occupancy_grid(backward_kernel, s.threads, s.smem, &s.grid) != cudaSuccess) {
+        s.n_smem = -1;
+        return s;
+    }
+    s.workspace = sizeof(float) * 2 * (size_t)(t->N + 2) * (size_t)s.grid;
+    return s;
+}
+
+pwl_status backward_launch(pwl_table t, const float* x, const float* gy, float* gx, float* g_values,
+                           float* g_knots, int64_t m, float* partials, int grid, cudaStream_t s)
+{
+    const BwdShape sh = backward_shape(t);
+    BwdArgs p{};
+    p.rec = t->rec_b;
+    p.hdr = t->hdr;
+    p.inv_h = t->inv_h;
+    p.N = (int)t->N;
+    p.K = (int)t->K;
+    p.n_smem = (int)sh.n_smem;
+    p.max_chain = 0;
+    p.a = t->a;
+    p.b = t->b;
+    p.inv_w = t->inv_w;
+    p.off = t->off;
+    const uintptr_t ax = reinterpret_cast<uintptr_t>(x), ag = reinterpret_cast<uintptr_t>(gy),
+                    ao = reinterpret_cast<uintptr_t>(gx);
+    p.nvec = ((ax | ag | ao) % 16 == 0) ? m / 4 : 0;
+    backward_kernel<<<grid, sh.threads, sh.smem, s>>>(p, x, gy, gx, m, partials);
+    PWL_CHECK_LAUNCH("backward_kernel");
+    if (g_values || g_knots) {
+        backward_reduce_kernel<<<(int)((t->N + 1 + 255) / 256), 256, 0, s>>>(partials, grid, (int)t->N,
+                                                                          t->slope, g_values, g_knots);
+        PWL_CHECK_LAUNCH("backward_reduce_kernel");
+    }
+    return PWL_OK;
+}
+
+}  // namespace pwl
+
+using namespace pwl;
+
+extern "C" {
+
+size_t pwl_eval_backward_workspace_size(pwl_table t)
+{
+    if (!t) return 0;
+    return backward_shape(t).workspace;
+}
+
+pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, float* d_gx,
+                             float* d_g_values, float* d_g_knots, int64_t m, void* d_workspace,
+                             size_t workspace_bytes, void* stream)
+{
+    clear_error();
+    if (!t) return fail(PWL_EINVAL, "table is NULL");
+    if (m < 0) return fail(PWL_EINVAL, "m must be >= 0");
+    if (m > 0 && (!d_x || !d_gy || !d_gx)) return fail(PWL_EINVAL, "x / gy / gx is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
+    const BwdShape sh = backward_shape(t);
+    if (sh.n_smem < 0)
+        return fail(PWL_ENOTSUP, "backward stages 12 (N+2) bytes of shared memory; N = %lld is too large (%s)",
+                    (long long)t->N, cudaGetErrorString(cudaGetLastError()));
+    if (!d_workspace || workspace_bytes < sh.workspace)
+        return fail(PWL_EINVAL, "workspace of %zu bytes needed (got %zu)", sh.workspace, workspace_bytes);
+    if (m == 0) return PWL_OK;
+    const int64_t units = m / 4 + 1;
+    const int grid = (int)std::min<int64_t>(sh.grid, std::max<int64_t>(1, (units + sh.threads - 1) / sh.threads));
+    return backward_launch(t, d_x, d_gy, d_gx, d_g_values, d_g_knots, m, static_cast<float*>(d_workspace),
+                           grid, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,208 @@
+// pwl_common.cuh -- internal declarations shared by the libpwl translation
+// units: error reporting, device properties, the analytic test functions,
+// the device table layout and the uniform cell index.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pwl.h"
+
+namespace pwl {
+
+// ---------------------------------------------------------------------------
+// host-side error handling
+// ---------------------------------------------------------------------------
+pwl_status fail(pwl_status s, const char* fmt, ...);
+pwl_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define PWL_CUDA_TRY(expr)                                              \
+    do {                                                                \
+        cudaError_t e_ = (expr);                                        \
+        if (e_ != cudaSuccess) return ::pwl::cuda_fail(e_, #expr);      \
+    } while (0)
+
+#define PWL_CHECK_LAUNCH(what)                                          \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return ::pwl::cuda_fail(e_, what);       \
+    } while (0)
+
+struct DeviceInfo {
+    int device;
+    int sms;
+    size_t smem_optin;   // max dynamic shared memory per block (opt-in)
+    size_t smem_per_sm;  // shared memory per multiprocessor
+    int max_threads_sm;
+};
+// properties of the current device (cached per device)
+const DeviceInfo& device_info();
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------------------
+// analytic functions: f and f'' (FP64 and FP32 versions)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FMath;
+template <>
+struct FMath<double> {
+    static __device__ __forceinline__ double ex(double x) { return exp(x); }
+    static __device__ __forceinline__ double bj0(double x) { return j0(x); }
+    static __device__ __forceinline__ double bj1(double x) { return j1(x); }
+    static __device__ __forceinline__ double pw(double x, double y) { return pow(x, y); }
+};
+template <>
+struct FMath<float> {
+    static __device__ __forceinline__ float ex(float x) { return expf(x); }
+    static __device__ __forceinline__ float bj0(float x) { return j0f(x); }
+    static __device__ __forceinline__ float bj1(float x) { return j1f(x); }
+    static __device__ __forceinline__ float pw(float x, float y) { return powf(x, y); }
+};
+
+// f(x) for the kinds of pwl_kind.
+template <typename T>
+__device__ __forceinline__ T func_value(const pwl_func& F, T x)
+{
+    using M = FMath<T>;
+    switch (F.kind) {
+    case PWL_F_GAUSSIAN: {
+        T u = (x - (T)F.p[1]) / (T)F.p[2];
+        return (T)F.p[0] * M::ex(T(-0.5) * u * u);
+    }
+    case PWL_F_LORENTZIAN: {
+        T u = (x - (T)F.p[1]) / (T)F.p[2];
+        return (T)F.p[0] / (T(1) + u * u);
+    }
+    case PWL_F_BESSEL_J0:
+        return (T)F.p[0] * M::bj0((T)F.p[1] * x);
+    case PWL_F_POLY: {
+        T s = T(0);
+        for (int k = 7; k >= 0; --k) s = s * x + (T)F.p[k];
+        return s;
+    }
+    case PWL_F_EXP:
+        return (T)F.p[0] * M::ex((T)F.p[1] * x);
+    }
+    return T(0);
+}
+
+// f''(x): Gaussian A (u^2-1)/s^2 e^{-u^2/2}; Lorentzian A (6u^2-2)/(g^2 (1+u^2)^3);
+// J0(alpha x): A alpha^2 (J1(z)/z - J0(z)) (Bessel's equation, limit 1/2 at 0);
+// polynomial and exponential by direct differentiation.
+template <typename T>
+__device__ __forceinline__ T func_second_derivative(const pwl_func& F, T x)
+{
+    using M = FMath<T>;
+    switch (F.kind) {
+    case PWL_F_GAUSSIAN: {
+        T s = (T)F.p[2];
+        T u = (x - (T)F.p[1]) / s;
+        return (T)F.p[0] * (u * u - T(1)) / (s * s) * M::ex(T(-0.5) * u * u);
+    }
+    case PWL_F_LORENTZIAN: {
+        T g = (T)F.p[2];
+        T u = (x - (T)F.p[1]) / g;
+        T q = T(1) + u * u;
+        return (T)F.p[0] * (T(6) * u * u - T(2)) / (g * g * q * q * q);
+    }
+    case PWL_F_BESSEL_J0: {
+        T al = (T)F.p[1];
+        T z = al * x;
+        T r = (fabs(z) < T(1e-8)) ? T(0.5) - z * z / T(16) : M::bj1(z) / z;
+        return (T)F.p[0] * al * al * (r - M::bj0(z));
+    }
+    case PWL_F_POLY: {
+        T s = T(0);
+        for (int k = 7; k >= 2; --k) s = s * x + (T)(k * (k - 1)) * (T)F.p[k];
+        return s;
+    }
+    case PWL_F_EXP:
+        return (T)F.p[0] * (T)F.p[1] * (T)F.p[1] * M::ex((T)F.p[1] * x);
+    }
+    return T(0);
+}
+
+// host-side descriptor validation
+pwl_status validate_func(const pwl_func* f);
+
+// ---------------------------------------------------------------------------
+// device table: FP32 knots, the uniform cell index and its records
+// ---------------------------------------------------------------------------
+// A record belongs to a knot j: {x_j, v_j, s_j, s_{j+1}} where s_j is the
+// slope of interval j = [x_{j-1}, x_j] (s_0 := s_1, s_{N+1} := s_N).  It gives
+// v exactly on [x_{j-1}, x_{j+1}]:  v(x) = v_j + (x - x_j) * (x < x_j ? s_j : s_{j+1}).
+// Cell c of the index holds the record of the first knot whose cell is c or,
+// if no knot falls in c, of the last knot before c.  When several knots share
+// a cell, the w field of a record is a link (a quiet NaN whose payload is the
+// index of the next knot's record in the chain area after the K cell
+// records) instead of s_{j+1}.  The backward records replace v_j by the
+// knot index j (as int bits).
+constexpr uint32_t kLinkTag = 0x7FC00000u;
+constexpr uint32_t kLinkMask = 0x003FFFFFu;
+
+__device__ __forceinline__ bool is_link(float w)
+{
+    return (__float_as_uint(w) & 0xFFC00000u) == kLinkTag;
+}
+__device__ __forceinline__ int link_index(float w) { return (int)(__float_as_uint(w) & kLinkMask); }
+__device__ __forceinline__ float make_link(int j) { return __uint_as_float(kLinkTag | (uint32_t)j); }
+
+// Cell of a point already clamped to [a, b]: c = trunc(x * inv_w + off)
+// with one rounding (fma), clamped to [0, K-1].  Monotone in x, which is
+// what makes the record lookup exact; the table builder uses this very
+// function on the knots.
+__device__ __forceinline__ int cell_of(float xc, float inv_w, float off, int K)
+{
+    int c = __float2int_rz(__fmaf_rn(xc, inv_w, off));
+    return min(max(c, 0), K - 1);
+}
+
+// clamp to [a, b] with NaN propagation
+__device__ __forceinline__ float clamp_nan(float x, float a, float b)
+{
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(a));
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(r), "f"(b));
+    return r;
+}
+
+// Device-side status of a table, written by the build kernels and read by
+// every kernel that uses the table (so that an asynchronous update needs no
+// host round trip).
+struct TableHeader {
+    int32_t status;      // bit 0: knots not strictly increasing; bit 1: non-finite knot or value;
+                         // bit 2: slope or reciprocal length not finite in FP32
+    uint32_t hmin_bits;  // shortest interval (positive float, ordered as uint)
+    int32_t n_chain;     // chain records after the K cell records
+    int32_t max_chain;   // most chain hops any query can need
+};
+
+}  // namespace pwl
+
+// The opaque handle behind pwl_table.
+struct pwl_table_s {
+    int device;
+    int64_t N, K;
+    int64_t n_chain;        // chain records at the last synchronous build
+    int64_t chain_reserve;  // chain records the streaming kernels stage in shared memory
+    int32_t dtype;
+    float a, b, inv_w, off;
+    void* buf_base;    // header, knots, values, slopes, build scratch
+    void* buf_rec;     // forward + backward records
+    pwl::TableHeader* hdr;
+    float* xk;
+    float* vk;
+    float* slope;
+    float* inv_h;
+    void* vstore;      // N+1 values in dtype
+    int* cj;           // build scratch: cell of every knot
+    int* cpos;         // build scratch: chain slot of every knot
+    float4* rec_f;
+    float4* rec_b;
+    cudaArray_t tex_array;
+    cudaTextureObject_t tex;
+};

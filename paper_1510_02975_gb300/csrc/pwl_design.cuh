@@ -1,0 +1,62 @@
+// pwl_design.cuh -- internal interface of the batched design and projection
+// kernels (one function is a batch of one).
+#pragma once
+
+#include "pwl_common.cuh"
+
+namespace pwl {
+
+constexpr int kMaxIntervals = 1048575;
+
+// F functions; function f owns knots koff[f] .. koff[f+1]-1 (N_f + 1 of them),
+// density cells moff[f] .. moff[f+1]-1 (M_f), chunks choff[f] .. choff[f+1]-1,
+// and G entries moff[f] + f .. moff[f+1] + f (M_f + 1).
+struct DesignPlan {
+    int F;
+    int precision;
+    const pwl_func* funcs;
+    const int64_t* koff;
+    const int64_t* moff;
+    const int64_t* choff;
+    int64_t total_knots, total_cells, total_chunks;
+    double* d;      // total_cells densities
+    double* G;      // total_cells + F cumulative values
+    double* csum;   // total_chunks partial sums
+    double* cbase;  // total_chunks exclusive chunk bases
+    double* stot;   // F totals (sum of d over the function)
+    double* knots;  // total_knots output
+};
+
+int64_t design_chunks(int64_t M);
+size_t design_scratch_bytes(int64_t F, int64_t total_cells, int64_t total_chunks);
+void design_carve_scratch(DesignPlan& p, void* scratch);
+pwl_status design_launch(const DesignPlan& p, cudaStream_t s);
+
+// Projection: F functions with knots at koff (device), values out.
+struct ProjectPlan {
+    int F;
+    int precision;
+    int form;
+    int max_rows;          // max over f of N_f + 1
+    int64_t total_knots;
+    int64_t total_intervals;
+    const pwl_func* funcs;
+    const int64_t* koff;
+    const double* knots;
+    double* values;
+    double2* lr;           // per interval: (int f phi_left, int f phi_right)
+    double* cr;            // 4 * total_knots doubles of solver scratch (used when rows do not fit smem)
+};
+
+struct GaussLegendre {
+    int Q;
+    double x[16];
+    double w[16];
+};
+const GaussLegendre& gauss_legendre_rule(int Q);
+
+size_t project_scratch_bytes(int64_t total_knots, int64_t total_intervals);
+void project_carve_scratch(ProjectPlan& p, void* scratch);
+pwl_status project_launch(const ProjectPlan& p, const GaussLegendre& gl, cudaStream_t s);
+
+}  // namespace pwl

@@ -1,0 +1,378 @@
+// pwl_table.cu -- device representation of a CPWL function: the inputs of
+// Algorithm 1 (knots x_samples and values v_samples) rounded to their storage
+// types, plus a uniform cell index over [x_0, x_N] whose records make the
+// search step of Algorithm 1 a single lookup.
+//
+// Build = two single-CTA kernels separated by one host synchronisation:
+//   table_round_kernel  FP64 -> FP32 knots, values -> dtype (-> FP32), slopes,
+//                       reciprocal lengths, validation and the shortest interval
+//   table_index_kernel  cell of every knot, chain positions, cell records
+// The host picks the cell count K between the two from the shortest
+// interval (cells no wider than it hold at most one knot).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "pwl_design.cuh"
+#include "pwl_table.cuh"
+
+namespace pwl {
+
+namespace {
+
+constexpr int kBuildThreads = 1024;
+
+
+__device__ __forceinline__ int block_exclusive_scan_int(int v, int* s_warp, int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int ws = (lane < W) ? s_warp[lane] : 0;
+        int wi = ws;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < W) s_warp[lane] = wi - ws;
+        if (lane == W - 1) s_warp[32] = wi;
+    }
+    __syncthreads();
+    int r = s_warp[warp] + incl - v;
+    *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) table_round_kernel(
+    const double* __restrict__ knots, const double* __restrict__ values, int N, int dtype, float* xk,
+    float* vk, void* vstore, float* slope, float* inv_h, TableHeader* hdr)
+{
+    __shared__ int s_status;
+    __shared__ unsigned s_hmin;
+    if (threadIdx.x == 0) {
+        s_status = 0;
+        s_hmin = 0x7f7fffffu;  // FLT_MAX
+    }
+    __syncthreads();
+    int st = 0;
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) {
+        const float xf = __double2float_rn(knots[i]);
+        const float vf = __double2float_rn(values[i]);
+        float vq = vf;
+        if (dtype == PWL_BF16) {
+            __nv_bfloat16 q = __float2bfloat16_rn(vf);
+            static_cast<__nv_bfloat16*>(vstore)[i] = q;
+            vq = __bfloat162float(q);
+        } else if (dtype == PWL_FP16) {
+            __half q = __float2half_rn(vf);
+            static_cast<__half*>(vstore)[i] = q;
+            vq = __half2float(q);
+        } else {
+            static_cast<float*>(vstore)[i] = vf;
+        }
+        if (!isfinite(xf) || !isfinite(vq)) st |= 2;
+        xk[i] = xf;
+        vk[i] = vq;
+    }
+    __syncthreads();
+    float hmin = 3.402823466e38f;
+    for (int i = 1 + threadIdx.x; i <= N; i += blockDim.x) {
+        const double h = (double)xk[i] - (double)xk[i - 1];
+        if (!(h > 0.0)) st |= 1;
+        const double s = ((double)vk[i] - (double)vk[i - 1]) / h;
+        const float fs = __double2float_rn(s);
+        const float fr = __double2float_rn(1.0 / h);
+        if (!isfinite(fs) || !isfinite(fr)) st |= 4;
+        slope[i] = fs;
+        inv_h[i] = fr;
+        hmin = fminf(hmin, (float)h);
+    }
+    if (threadIdx.x == 0) {
+        // end conventions: s_0 := s_1, s_{N+1} := s_N (same for 1/h)
+        const double h1 = (double)xk[1] - (double)xk[0];
+        const double hN = (double)xk[N] - (double)xk[N - 1];
+        slope[0] = __double2float_rn(((double)vk[1] - (double)vk[0]) / h1);
+        inv_h[0] = __double2float_rn(1.0 / h1);
+        slope[N + 1] = __double2float_rn(((double)vk[N] - (double)vk[N - 1]) / hN);
+        inv_h[N + 1] = __double2float_rn(1.0 / hN);
+    }
+    if (st) atomicOr(&s_status, st);
+    if (hmin > 0.0f) atomicMin(&s_hmin, __float_as_uint(hmin));
+    else atomicMin(&s_hmin, 0u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        hdr->status = s_status;
+        hdr->hmin_bits = s_hmin;
+        hdr->n_chain = 0;
+        hdr->max_chain = 0;
+    }
+}
+
+// first index j in [0, n) with c[j] >= v (n if none)
+__device__ __forceinline__ int lower_bound_int(const int* c, int n, int v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (c[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) table_index_kernel(
+    int N, int K, float inv_w, float off, const float* __restrict__ xk, const float* __restrict__ vk,
+    const float* __restrict__ slope, int* cj, int* cpos, float4* rec_f, float4* rec_b,
+    TableHeader* hdr)
+{
+    __shared__ int s_warp[33];
+    __shared__ int s_maxchain;
+    if (threadIdx.x == 0) s_maxchain = 0;
+    for (int j = threadIdx.x; j <= N; j += blockDim.x) cj[j] = cell_of(xk[j], inv_w, off, K);
+    __syncthreads();
+    int carry = 0;
+    for (int base = 0; base <= N; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        const int flag = (j <= N && j > 0 && cj[j] == cj[j - 1]) ? 1 : 0;
+        int tot;
+        const int ex = block_exclusive_scan_int(flag, s_warp, &tot);
+        if (j <= N) cpos[j] = carry + ex;
+        carry += tot;
+    }
+    const int n_chain = carry;
+    __syncthreads();
+    // records of the K cells
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        const int lb = lower_bound_int(cj, N + 1, c);
+        int j;
+        bool chained = false;
+        if (lb <= N && cj[lb] == c) {
+            j = lb;
+            chained = (j < N && cj[j + 1] == c);
+        } else {
+            j = lb - 1;
+        }
+        const float w = chained ? make_link(K + cpos[j + 1]) : slope[j + 1];
+        rec_f[c] = make_float4(xk[j], vk[j], slope[j], w);
+        rec_b[c] = make_float4(xk[j], __int_as_float(j), slope[j], w);
+    }
+    // chain records: knots that share their cell with the previous knot
+    int my_max = 0;
+    for (int j = 1 + threadIdx.x; j <= N; j += blockDim.x) {
+        if (cj[j] != cj[j - 1]) continue;
+        const bool chained = (j < N && cj[j + 1] == cj[j]);
+        const float w = chained ? make_link(K + cpos[j + 1]) : slope[j + 1];
+        const int idx = K + cpos[j];
+        rec_f[idx] = make_float4(xk[j], vk[j], slope[j], w);
+        rec_b[idx] = make_float4(xk[j], __int_as_float(j), slope[j], w);
+        my_max = max(my_max, j - lower_bound_int(cj, N + 1, cj[j]));
+    }
+    if (my_max) atomicMax(&s_maxchain, my_max);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        hdr->n_chain = n_chain;
+        hdr->max_chain = s_maxchain;
+    }
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int64_t choose_cells(int64_t N, float a, float b, float hmin, int64_t requested)
+{
+    const DeviceInfo& di = device_info();
+    const int64_t link_cap = (int64_t)kLinkMask - N - 2;
+    // as many records as one CTA can stage next to nothing else (forward
+    // kernel), leaving 8 KB for the chain records of the cells that overflow;
+    // the forward kernel relies on every cell record being staged
+    const int64_t cap = std::min<int64_t>((int64_t)((di.smem_optin - 8192) / sizeof(float4)), link_cap);
+    if (requested > 0) return std::min<int64_t>(requested, cap);
+    // cells no wider than the shortest interval: at most one knot per cell
+    const double need = ceil(((double)b - (double)a) / (double)hmin) + 1.0;
+    int64_t K = (int64_t)std::min<double>(need, (double)cap);
+    return std::max<int64_t>(K, 1);
+}
+
+namespace {
+
+// Launches both build kernels for a table whose buffers and K are set.
+pwl_status launch_build(pwl_table t, const double* d_knots, const double* d_values, bool index_only,
+                        cudaStream_t s)
+{
+    const int N = (int)t->N;
+    if (!index_only) {
+        table_round_kernel<<<1, kBuildThreads, 0, s>>>(d_knots, d_values, N, t->dtype, t->xk, t->vk, t->vstore,
+                                                       t->slope, t->inv_h, t->hdr);
+        PWL_CHECK_LAUNCH("table_round_kernel");
+    }
+    table_index_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->K, t->inv_w, t->off, t->xk, t->vk, t->slope,
+                                                   t->cj, t->cpos, t->rec_f, t->rec_b, t->hdr);
+    PWL_CHECK_LAUNCH("table_index_kernel");
+    return PWL_OK;
+}
+
+pwl_status status_error(const TableHeader& h)
+{
+    if (h.status & 1) return fail(PWL_EINVAL, "knots are not strictly increasing after rounding to FP32");
+    if (h.status & 2) return fail(PWL_EINVAL, "a knot or value is not finite");
+    if (h.status & 4) return fail(PWL_EINVAL, "a slope or reciprocal length overflows FP32");
+    return PWL_OK;
+}
+
+}  // namespace
+
+}  // namespace pwl
+
+using namespace pwl;
+
+extern "C" {
+
+pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_t n_intervals,
+                           int32_t value_dtype, int64_t k_cells, pwl_table* out, void* stream)
+{
+    clear_error();
+    if (!out) return fail(PWL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d_knots || !d_values) return fail(PWL_EINVAL, "d_knots / d_values is NULL");
+    if (n_intervals < 1 || n_intervals > kMaxIntervals)
+        return fail(PWL_EINVAL, "n_intervals must be in [1, %d] (got %lld)", kMaxIntervals,
+                    (long long)n_intervals);
+    if (value_dtype != PWL_FP32 && value_dtype != PWL_BF16 && value_dtype != PWL_FP16)
+        return fail(PWL_EINVAL, "unknown value dtype %d", value_dtype);
+    if (k_cells < 0) return fail(PWL_EINVAL, "k_cells must be >= 0");
+    const int N = (int)n_intervals;
+    cudaStream_t s = as_stream(stream);
+
+    pwl_table_s* t = new (std::nothrow) pwl_table_s();
+    if (!t) return fail(PWL_ENOMEM, "host allocation failed");
+    memset(t, 0, sizeof(*t));
+    cudaGetDevice(&t->device);
+    t->N = N;
+    t->dtype = value_dtype;
+    const size_t n1 = (size_t)N + 1, n2 = (size_t)N + 2;
+    const size_t o_xk = 256;
+    const size_t o_vk = o_xk + align256(4 * n1);
+    const size_t o_sl = o_vk + align256(4 * n1);
+    const size_t o_ih = o_sl + align256(4 * n2);
+    const size_t o_vs = o_ih + align256(4 * n2);
+    const size_t o_cj = o_vs + align256(4 * n1);
+    const size_t o_cp = o_cj + align256(4 * n1);
+    const size_t total = o_cp + align256(4 * n1);
+    cudaError_t e = cudaMalloc(&t->buf_base, total);
+    if (e != cudaSuccess) {
+        delete t;
+        return cuda_fail(e, "cudaMalloc(table)");
+    }
+    char* base = static_cast<char*>(t->buf_base);
+    t->hdr = reinterpret_cast<TableHeader*>(base);
+    t->xk = reinterpret_cast<float*>(base + o_xk);
+    t->vk = reinterpret_cast<float*>(base + o_vk);
+    t->slope = reinterpret_cast<float*>(base + o_sl);
+    t->inv_h = reinterpret_cast<float*>(base + o_ih);
+    t->vstore = base + o_vs;
+    t->cj = reinterpret_cast<int*>(base + o_cj);
+    t->cpos = reinterpret_cast<int*>(base + o_cp);
+
+    auto bail = [&](pwl_status st) {
+        pwl_table_destroy(t);
+        return st;
+    };
+
+    table_round_kernel<<<1, kBuildThreads, 0, s>>>(d_knots, d_values, N, value_dtype, t->xk, t->vk,
+                                                   t->vstore, t->slope, t->inv_h, t->hdr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "table_round_kernel"));
+    TableHeader h{};
+    float ab[2];
+    if ((e = cudaMemcpyAsync(&h, t->hdr, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&ab[0], t->xk, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&ab[1], t->xk + N, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return bail(cuda_fail(e, "table build (rounding pass)"));
+    pwl_status st = status_error(h);
+    if (st != PWL_OK) return bail(st);
+    float hmin;
+    memcpy(&hmin, &h.hmin_bits, 4);
+    t->a = ab[0];
+    t->b = ab[1];
+    t->K = choose_cells(N, t->a, t->b, hmin, k_cells);
+    // the cell function: c = trunc(fma(x, inv_w, off)), inv_w = K / (b - a)
+    t->inv_w = (float)t->K / (t->b - t->a);
+    t->off = -t->a * t->inv_w;
+    const size_t nrec = (size_t)t->K + n1;
+    if ((e = cudaMalloc(&t->buf_rec, 2 * align256(sizeof(float4) * nrec))) != cudaSuccess)
+        return bail(cuda_fail(e, "cudaMalloc(records)"));
+    t->rec_f = static_cast<float4*>(t->buf_rec);
+    t->rec_b = reinterpret_cast<float4*>(static_cast<char*>(t->buf_rec) + align256(sizeof(float4) * nrec));
+    if ((st = launch_build(t, d_knots, d_values, true, s)) != PWL_OK) return bail(st);
+    if ((e = cudaMemcpyAsync(&h, t->hdr, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return bail(cuda_fail(e, "table build (index pass)"));
+    t->n_chain = h.n_chain;
+    // shared-memory room for the chains of this build and of later updates
+    // that move a few knots (further chain records are read from global memory)
+    t->chain_reserve = std::min<int64_t>((int64_t)n1, t->n_chain + 64);
+    *out = t;
+    return PWL_OK;
+}
+
+pwl_status pwl_table_update(pwl_table t, const double* d_knots, const double* d_values, void* stream)
+{
+    clear_error();
+    if (!t) return fail(PWL_EINVAL, "table is NULL");
+    if (!d_knots || !d_values) return fail(PWL_EINVAL, "d_knots / d_values is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
+    return launch_build(t, d_knots, d_values, false, as_stream(stream));
+}
+
+pwl_status pwl_table_check(pwl_table t, void* stream)
+{
+    clear_error();
+    if (!t) return fail(PWL_EINVAL, "table is NULL");
+    TableHeader h{};
+    cudaStream_t s = as_stream(stream);
+    PWL_CUDA_TRY(cudaMemcpyAsync(&h, t->hdr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PWL_CUDA_TRY(cudaStreamSynchronize(s));
+    return status_error(h);
+}
+
+pwl_status pwl_table_destroy(pwl_table t)
+{
+    if (!t) return PWL_OK;
+    if (t->tex) cudaDestroyTextureObject(t->tex);
+    if (t->tex_array) cudaFreeArray(t->tex_array);
+    if (t->buf_rec) cudaFree(t->buf_rec);
+    if (t->buf_base) cudaFree(t->buf_base);
+    delete t;
+    return PWL_OK;
+}
+
+pwl_status pwl_table_get_info(pwl_table t, pwl_table_info* info)
+{
+    clear_error();
+    if (!t || !info) return fail(PWL_EINVAL, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n_intervals = t->N;
+    info->k_cells = t->K;
+    info->n_chain = t->n_chain;
+    info->value_dtype = t->dtype;
+    info->a = t->a;
+    info->b = t->b;
+    info->d_knots = t->xk;
+    info->d_values = t->vstore;
+    info->eval_smem_bytes = eval_smem_bytes(t);
+    info->backward_smem_bytes = backward_smem_bytes(t);
+    return PWL_OK;
+}
+
+}  // extern "C"

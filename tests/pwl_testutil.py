@@ -1,0 +1,35 @@
+"""Helpers shared by the GPU parity tests: rounding of tables to the storage
+types the library uses, and tolerances.
+
+Tolerances (from the arithmetic):
+  FP32 evaluation of the same CPWL table: |y - y_ref| <= 5e-7 max|y_ref|
+    (the FP32 slope has relative error 2^-24, the FMA one more rounding:
+     both <= 2^-24 |v_i - v_{i-1}| + 2^-24 |y|, well inside 5e-7 max|y|).
+  FP64 design and projection: knots within 1e-12 (b - a); values within
+    1e-12 max|v| (different summation orders and cyclic reduction vs Thomas).
+  Table gradients (FP32 accumulation): within 1e-5 of the sum of the
+    absolute values of the accumulated terms (FP64 reference).
+"""
+import numpy as np
+
+EVAL_REL = 5e-7
+DESIGN_REL = 1e-12
+VALUES_REL = 1e-12
+GRAD_REL = 1e-5
+
+
+def round_values(v, dtype: str) -> np.ndarray:
+    """FP64 values -> FP32 (round to nearest) -> 16-bit type, widened back."""
+    import torch
+    v32 = np.asarray(v, dtype=np.float64).astype(np.float32)
+    if dtype == "fp32":
+        return v32.astype(np.float64)
+    if dtype == "fp16":
+        return v32.astype(np.float16).astype(np.float64)
+    if dtype == "bf16":
+        return torch.from_numpy(v32).to(torch.bfloat16).to(torch.float64).numpy()
+    raise ValueError(dtype)
+
+
+def round_knots(k) -> np.ndarray:
+    return np.asarray(k, dtype=np.float64).astype(np.float32).astype(np.float64)

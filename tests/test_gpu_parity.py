@@ -1,0 +1,262 @@
+"""GPU vs oracle parity through the C ABI: design (Eqs. 16-18), vertex
+values (Eqs. 3-6), table evaluation (Algorithm 1) and its backward, on sizes
+the oracle finishes quickly that still span many tiles and a ragged tail."""
+import numpy as np
+import pytest
+
+import oracle
+from pwl_testutil import DESIGN_REL, EVAL_REL, GRAD_REL, VALUES_REL, round_knots, round_values
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pwl():
+    import paper_1510_02975_gb300 as m
+    from paper_1510_02975_gb300 import _build
+    _build.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def workloads():
+    from paper_1510_02975_gb300 import workloads as w
+    return w
+
+
+FUNCS = ["gaussian", "lorentzian", "bessel_j0"]
+
+
+@pytest.mark.parametrize("name", FUNCS)
+@pytest.mark.parametrize("N", [1, 2, 63, 256, 1024, 4096])
+def test_design_matches_oracle(pwl, workloads, name, N):
+    f = workloads.PAPER_FUNCTIONS[name]
+    got = pwl.pwl_design(f, N).cpu().numpy()
+    ref = oracle.design(f, N)
+    assert np.abs(got - ref).max() <= DESIGN_REL * (f["b"] - f["a"])
+    assert got[0] == f["a"] and got[-1] == f["b"]
+    assert np.all(np.diff(got) > 0)
+
+
+@pytest.mark.parametrize("M", [1, 7, 2047, 2048, 2049, 5000])
+def test_design_cells_ragged(pwl, workloads, M):
+    f = workloads.LORENTZIAN
+    N = 40
+    got = pwl.pwl_design(f, N, M).cpu().numpy()
+    ref = oracle.design(f, N, M)
+    assert np.abs(got - ref).max() <= DESIGN_REL * (f["b"] - f["a"])
+
+
+def test_design_linear_function_is_uniform(pwl):
+    f = {"kind": "poly", "a": -1.0, "b": 2.0, "p": [3.0, -0.5]}
+    got = pwl.pwl_design(f, 12).cpu().numpy()
+    assert np.allclose(got, -1.0 + np.arange(13) * 0.25, atol=1e-15)
+
+
+def test_design_fp32_density_mode(pwl, workloads):
+    # FP32 integrand: knots move by about (FP32 rounding of d) / d * h
+    for name in FUNCS:
+        f = workloads.PAPER_FUNCTIONS[name]
+        N = 1024
+        got = pwl.pwl_design(f, N, 0, "fp32").cpu().numpy()
+        ref = oracle.design(f, N)
+        h = np.diff(ref).min()
+        assert np.abs(got - ref).max() <= 1e-3 * h
+
+
+@pytest.mark.parametrize("name", FUNCS)
+@pytest.mark.parametrize("form", ["interp", "project"])
+@pytest.mark.parametrize("N", [1, 3, 63, 1024, 4096])
+def test_values_match_oracle(pwl, workloads, name, form, N):
+    f = workloads.PAPER_FUNCTIONS[name]
+    knots = pwl.pwl_design(f, N)
+    kn = knots.cpu().numpy()
+    got = pwl.pwl_project(f, knots, form).cpu().numpy()
+    ref = oracle.values(f, kn, form)
+    assert np.abs(got - ref).max() <= VALUES_REL * np.abs(ref).max()
+
+
+def test_projection_large_n_global_solver(pwl, workloads):
+    # N + 1 > rows that fit in shared memory: the solver runs on global scratch
+    f = workloads.BESSEL_J0
+    N = 20000
+    knots = pwl.pwl_design(f, N)
+    kn = knots.cpu().numpy()
+    got = pwl.pwl_project(f, knots, "project").cpu().numpy()
+    ref = oracle.values(f, kn, "project")
+    assert np.abs(got - ref).max() <= VALUES_REL * np.abs(ref).max()
+
+
+def _table_and_ref(pwl, f, N, form="project", dtype="fp32", k_cells=0):
+    knots = pwl.pwl_design(f, N)
+    vals = pwl.pwl_project(f, knots, form)
+    t = pwl.Table(knots, vals, dtype, k_cells)
+    xk = round_knots(knots.cpu().numpy())
+    vk = round_values(vals.cpu().numpy(), dtype)
+    return t, xk, vk
+
+
+def _check_eval(y, xk, vk, x):
+    ref = oracle.evaluate(xk, vk, x.cpu().numpy().astype(np.float64))
+    got = y.cpu().numpy().astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(nan, np.isnan(got))
+    assert np.abs(got[~nan] - ref[~nan]).max(initial=0.0) <= EVAL_REL * np.abs(ref[~nan]).max(initial=1.0)
+
+
+@pytest.mark.parametrize("name", FUNCS)
+@pytest.mark.parametrize("N", [1, 63, 256, 1024, 4096])
+def test_eval_matches_oracle(pwl, workloads, name, N):
+    f = workloads.PAPER_FUNCTIONS[name]
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 20) + 3  # several tiles and a ragged tail
+    x = workloads.uniform_queries(f, m, seed=1)
+    _check_eval(t(x), xk, vk, x)
+    xn = workloads.normal_queries(f, m, seed=2)
+    _check_eval(t(xn), xk, vk, xn)
+    t.close()
+
+
+def test_eval_small_case_both_forms(pwl, workloads):
+    s = workloads.SMALL
+    for form in ("interp", "project"):
+        t, xk, vk = _table_and_ref(pwl, s["func"], s["n_intervals"], form)
+        x = workloads.uniform_queries(s["func"], s["m"], s["seed"])
+        _check_eval(t(x), xk, vk, x)
+        t.close()
+
+
+@pytest.mark.parametrize("k_cells", [1, 3, 17, 64, 1000, 9000])
+def test_eval_any_cell_count(pwl, workloads, k_cells):
+    # few cells force chains of many knots per cell; many cells none
+    f = workloads.LORENTZIAN
+    t, xk, vk = _table_and_ref(pwl, f, 300, k_cells=k_cells)
+    assert t.info["k_cells"] == k_cells
+    x = workloads.uniform_queries(f, 100003, seed=7)
+    _check_eval(t(x), xk, vk, x)
+    t.close()
+
+
+def test_eval_edge_cases(pwl, workloads):
+    f = workloads.BESSEL_J0
+    t, xk, vk = _table_and_ref(pwl, f, 257)
+    x = np.concatenate([xk, [-1e30, -1.0, 0.0, 50.0, 51.0, 1e30, np.nan, np.inf, -np.inf],
+                        0.5 * (xk[1:] + xk[:-1]), np.nextafter(xk.astype(np.float32), np.float32(np.inf))])
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    _check_eval(t(xt), xk, vk, xt)
+    # exact at the knots
+    yk = t(torch.tensor(xk, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert np.array_equal(yk.astype(np.float64), vk)
+    # m = 0, 1, 3 and unaligned pointers
+    for m in (0, 1, 3, 5):
+        xs = torch.linspace(-1, 51, m, device="cuda")
+        _check_eval(t(xs), xk, vk, xs)
+    big = workloads.uniform_queries(f, 4099, seed=3)
+    for off_x, off_y in ((1, 1), (1, 2), (3, 0), (0, 2)):
+        xs = big[off_x:off_x + 4000]
+        out = torch.empty(4100, device="cuda")
+        ys = out[off_y:off_y + 4000]
+        pwl.pwl_eval(t.handle, xs, ys)
+        _check_eval(ys, xk, vk, xs)
+    # in place
+    xs = big.clone()
+    pwl.pwl_eval(t.handle, xs, xs)
+    _check_eval(xs, xk, vk, big)
+    t.close()
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp16"])
+def test_reduced_precision_tables(pwl, workloads, dtype):
+    for name in FUNCS:
+        f = workloads.PAPER_FUNCTIONS[name]
+        t, xk, vk = _table_and_ref(pwl, f, 1024, dtype=dtype)
+        x = workloads.uniform_queries(f, 1 << 18, seed=1)
+        _check_eval(t(x), xk, vk, x)
+        t.close()
+
+
+@pytest.mark.parametrize("io", ["bf16", "fp16"])
+def test_reduced_precision_io(pwl, workloads, io):
+    tdt = {"bf16": torch.bfloat16, "fp16": torch.float16}[io]
+    f = workloads.GAUSSIAN
+    t, xk, vk = _table_and_ref(pwl, f, 1024)
+    x = workloads.uniform_queries(f, (1 << 18) + 5, seed=1).to(tdt)
+    y = t(x)
+    ref = oracle.evaluate(xk, vk, x.float().cpu().numpy().astype(np.float64))
+    got = y.float().cpu().numpy().astype(np.float64)
+    # output rounded once to the 16-bit type: half an ulp of |y| plus the FP32 bound
+    # (relative ulp <= 2^-7 for bf16, 2^-10 for fp16; 2^-24 covers fp16 subnormals)
+    ulp = {"bf16": 2.0**-7, "fp16": 2.0**-10}[io]
+    assert np.all(np.abs(got - ref) <= 0.5 * ulp * np.abs(ref) * 1.0001 + EVAL_REL * np.abs(ref).max() + 2.0**-24)
+    t.close()
+
+
+def test_variant_binary_search(pwl, workloads):
+    for name in FUNCS:
+        f = workloads.PAPER_FUNCTIONS[name]
+        t, xk, vk = _table_and_ref(pwl, f, 1024)
+        x = workloads.uniform_queries(f, (1 << 18) + 1, seed=1)
+        _check_eval(t.variant(0, x), xk, vk, x)
+        t.close()
+
+
+def test_variant_texture_filter(pwl, workloads):
+    # the filter weight has 8 fractional bits: |err| <= |v_i - v_{i-1}| / 2^8
+    # (plus FP32 rounding of the coordinate and the result)
+    for name in FUNCS:
+        f = workloads.PAPER_FUNCTIONS[name]
+        t, xk, vk = _table_and_ref(pwl, f, 1024)
+        x = workloads.uniform_queries(f, (1 << 18) + 1, seed=1)
+        y = t.variant(1, x).cpu().numpy().astype(np.float64)
+        xs = x.cpu().numpy().astype(np.float64)
+        ref = oracle.evaluate(xk, vk, xs)
+        i = np.clip(np.searchsorted(xk, xs, side="right"), 1, len(xk) - 1)
+        dv = np.abs(vk[i] - vk[i - 1])
+        assert np.all(np.abs(y - ref) <= dv / 256.0 + 1e-6 * np.abs(vk).max())
+        t.close()
+
+
+@pytest.mark.parametrize("name", FUNCS)
+@pytest.mark.parametrize("N", [1, 5, 256, 4096])
+def test_backward_matches_oracle(pwl, workloads, name, N):
+    f = workloads.PAPER_FUNCTIONS[name]
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 18) + 7
+    x = workloads.uniform_queries(f, m, seed=1)
+    # some queries outside the domain and exactly at knots
+    x[:100] = float(f["a"]) - 1.0
+    x[100:200] = float(f["b"]) + 1.0
+    x[200:200 + len(xk)] = torch.tensor(xk, dtype=torch.float32, device="cuda")
+    gy = workloads.upstream_grad((m,), seed=5)
+    gv = torch.zeros(N + 1, device="cuda")
+    gk = torch.zeros(N + 1, device="cuda")
+    gx = t.backward(x, gy, None, gv, gk)
+    rgx, rgv, rgk, rgva, rgka = oracle.evaluate_grad(xk, vk, x.cpu().numpy().astype(np.float64),
+                                                     gy.cpu().numpy().astype(np.float64))
+    assert np.abs(gx.cpu().numpy() - rgx).max() <= EVAL_REL * np.abs(rgx).max()
+    assert np.all(np.abs(gv.cpu().numpy() - rgv) <= GRAD_REL * rgva + 1e-30)
+    assert np.all(np.abs(gk.cpu().numpy() - rgk) <= GRAD_REL * rgka + 1e-30)
+    # a second call agrees to FP32 rounding of the in-CTA sums
+    gv2 = torch.zeros_like(gv)
+    gk2 = torch.zeros_like(gk)
+    gx2 = t.backward(x, gy, None, gv2, gk2)
+    assert torch.equal(gx, gx2)
+    assert np.all(np.abs((gv2 - gv).cpu().numpy()) <= GRAD_REL * rgva + 1e-30)
+    assert np.all(np.abs((gk2 - gk).cpu().numpy()) <= GRAD_REL * rgka + 1e-30)
+    t.close()
+
+
+def test_invalid_arguments_are_rejected(pwl, workloads):
+    from paper_1510_02975_gb300 import PwlError
+    bad = dict(workloads.GAUSSIAN, a=1.0, b=0.0)
+    with pytest.raises(PwlError):
+        pwl.pwl_design(bad, 10)
+    k = torch.tensor([0.0, 1.0, 1.0, 2.0], dtype=torch.float64, device="cuda")
+    with pytest.raises(PwlError):
+        pwl.Table(k, torch.zeros_like(k))
+    k = torch.tensor([0.0, 1.0, 2.0], dtype=torch.float64, device="cuda")
+    v = torch.tensor([0.0, float("nan"), 2.0], dtype=torch.float64, device="cuda")
+    with pytest.raises(PwlError):
+        pwl.Table(k, v)
