@@ -228,6 +228,24 @@ pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, f
                              float* d_g_values, float* d_g_knots, int64_t m, void* d_workspace,
                              size_t workspace_bytes, void* stream);
 
+/* pwl_eval_backward for callers that cannot allocate device memory (the
+ * paper has no counterpart; this is a library concern): real-time loops that
+ * fix their memory at start-up, code called back from a host framework that
+ * owns all device memory, and callers with no workspace to lend.  It takes
+ * the same inputs and outputs as pwl_eval_backward but no workspace: its
+ * per-CTA partial sums go to a static device array of 2^21 floats (8 MiB)
+ * that every GPU which loads the library holds until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - N must satisfy 2 (N + 2) * (SM count) <= 2^21 (N <= 6896 on a 152-SM
+ *     GB300); larger tables are rejected with PWL_EINVAL and a message.
+ *   - Every call shares the one array and overwrites what it uses, so calls
+ *     whose work overlaps on the GPU (other streams, other threads) race:
+ *     serialise them.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.        */
+pwl_status pwl_eval_backward_noalloc(pwl_table t, const float* d_x, const float* d_gy, float* d_gx,
+                                     float* d_g_values, float* d_g_knots, int64_t m, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ from ._capi import DTYPES, FORMS, KINDS, PRECISIONS, PwlError, PwlTableInfo, che
 
 __all__ = [
     "PwlError", "pwl_design", "pwl_project", "pwl_table_build", "pwl_table_update", "pwl_table_check", "pwl_table_destroy", "pwl_table_get_info",
-    "pwl_eval", "pwl_eval_variant", "pwl_eval_backward", "Table", "design", "project", "PWLFunction",
+    "pwl_eval", "pwl_eval_variant", "pwl_eval_backward", "pwl_eval_backward_noalloc", "Table", "design", "project", "PWLFunction",
     "KINDS", "FORMS", "DTYPES", "PRECISIONS",
 ]
 
@@ -177,6 +177,21 @@ def pwl_eval_backward(handle, x, gy, gx=None, g_values=None, g_knots=None, works
     check(lib.pwl_eval_backward(ctypes.c_void_p(handle), _ptr(x), _ptr(gy), _ptr(gx), _ptr(g_values),
                                 _ptr(g_knots), x.numel(), _ptr(workspace), workspace.numel(), _stream(stream)),
           "pwl_eval_backward")
+    return gx
+
+
+def pwl_eval_backward_noalloc(handle, x, gy, gx=None, g_values=None, g_knots=None, stream=None):
+    """pwl_eval_backward without a workspace: the partial sums go to the
+    library's static device array (for callers that cannot allocate; calls
+    that overlap on the GPU race)."""
+    torch = _torch()
+    _require(x, torch.float32, "x")
+    _require(gy, torch.float32, "gy", x.numel())
+    if gx is None:
+        gx = torch.empty_like(x)
+    _require(gx, torch.float32, "gx", x.numel())
+    check(load().pwl_eval_backward_noalloc(ctypes.c_void_p(handle), _ptr(x), _ptr(gy), _ptr(gx), _ptr(g_values),
+                                           _ptr(g_knots), x.numel(), _stream(stream)), "pwl_eval_backward_noalloc")
     return gx
 
 

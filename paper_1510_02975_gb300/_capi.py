@@ -61,6 +61,7 @@ SIGNATURES = {
     "pwl_eval_variant": (_ST, [_P, _I32, _P, _P, _I64, _P]),
     "pwl_eval_backward_workspace_size": (_SZ, [_P]),
     "pwl_eval_backward": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P, _SZ, _P]),
+    "pwl_eval_backward_noalloc": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P]),
 }
 
 _lib = None

@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pwl_backward.cuh"
 
@@ -225,11 +226,80 @@ pwl_status backward_launch(pwl_table t, const float* x, const float* gy, float* 
     return PWL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Backward without any allocation: the per-CTA partial sums live in a
+// fixed, file-scope device array instead of a caller workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 2^21 floats (8 MiB) per GPU that loads the library, held until exit.
+constexpr size_t kStaticPartials = (size_t)1 << 21;
+static __device__ __align__(256) float g_static_partials[kStaticPartials];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_partials on `dev` (the current device).  The
+// first call per device looks it up; in host code the array's name is only
+// a host-side stand-in, never a device address.
+pwl_status static_partials(int dev, float** out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail(PWL_ENOTSUP, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_partials)");
+        g_static_addr[dev] = static_cast<float*>(p);
+    }
+    *out = g_static_addr[dev];
+    return PWL_OK;
+}
+
+}  // namespace
+
 }  // namespace pwl
 
 using namespace pwl;
 
 extern "C" {
+
+pwl_status pwl_eval_backward_noalloc(pwl_table t, const float* d_x, const float* d_gy, float* d_gx,
+                                     float* d_g_values, float* d_g_knots, int64_t m, void* stream)
+{
+    clear_error();
+    if (!t) return fail(PWL_EINVAL, "table is NULL");
+    if (m < 0) return fail(PWL_EINVAL, "m must be >= 0");
+    if (m > 0 && (!d_x || !d_gy || !d_gx)) return fail(PWL_EINVAL, "x / gy / gx is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
+    // device_info() of this device is already cached: pwl_table_build used it
+    const BwdShape sh = backward_shape(t);
+    if (sh.n_smem < 0)
+        return fail(PWL_ENOTSUP, "backward stages 12 (N+2) bytes of shared memory; N = %lld is too large",
+                    (long long)t->N);
+    const int sms = device_info().sms;
+    const int64_t row = 2 * (t->N + 2);
+    const int64_t rows = (int64_t)(kStaticPartials / (size_t)row);
+    if (rows < sms)
+        return fail(PWL_EINVAL,
+                    "N = %lld too large for the static scratch of %zu floats: it needs one row of 2 (N + 2) "
+                    "floats per SM, so N <= %lld on this %d-SM GPU",
+                    (long long)t->N, kStaticPartials, (long long)(kStaticPartials / (2 * (size_t)sms)) - 2, sms);
+    float* partials = nullptr;
+    pwl_status st = static_partials(dev, &partials);
+    if (st != PWL_OK) return st;
+    if (m == 0) return PWL_OK;
+    const int64_t units = m / 4 + 1;
+    int64_t grid = std::min<int64_t>(sh.grid, rows);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, (units + sh.threads - 1) / sh.threads));
+    // every launched CTA overwrites its whole row before the reduction reads
+    // it, so the array's leftover contents from earlier calls do not matter
+    return backward_launch(t, d_x, d_gy, d_gx, d_g_values, d_g_knots, m, partials, (int)grid,
+                           as_stream(stream));
+}
 
 size_t pwl_eval_backward_workspace_size(pwl_table t)
 {
