@@ -56,6 +56,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=21, help="oracle queries per (table, set)")
     ap.add_argument("--fwd-bwd-steps", type=int, default=3)
+    ap.add_argument("--report", default=None, choices=[None, "variants"],
+                    help="variants: per-table throughput of every evaluation path and the error of each "
+                         "vertex-table precision (one JSON line)")
+    ap.add_argument("--k-cells", type=int, default=0, help="cell count of the tables in --report variants")
     return ap.parse_args()
 
 
@@ -223,17 +227,41 @@ class Workload:
                 tp = pwl.Table(kn, vp)
                 self.items.append((fi, N, kn, vi, vp, wsd, wsp, ti, tp))
         torch.cuda.synchronize()
+        self.capture_design()
         self.evals_per_step = len(self.items) * len(FORMS) * 2 * self.m
 
-    def design_and_tables(self):
+    def _design_item(self, item):
         pwl = self.pwl
-        for fi, N, kn, vi, vp, wsd, wsp, ti, tp in self.items:
-            f = self.funcs[fi]
-            pwl.pwl_design(f, N, 0, "fp64", knots=kn, workspace=wsd)
-            pwl.pwl_project(f, kn, "interp", values=vi, workspace=wsp)
-            pwl.pwl_project(f, kn, "project", values=vp, workspace=wsp)
-            ti.update(kn, vi)
-            tp.update(kn, vp)
+        fi, N, kn, vi, vp, wsd, wsp, ti, tp = item
+        f = self.funcs[fi]
+        pwl.pwl_design(f, N, 0, "fp64", knots=kn, workspace=wsd)
+        pwl.pwl_project(f, kn, "interp", values=vi, workspace=wsp)
+        pwl.pwl_project(f, kn, "project", values=vp, workspace=wsp)
+        ti.update(kn, vi)
+        tp.update(kn, vp)
+
+    def capture_design(self):
+        """Design, both projections and both table rebuilds of every
+        (function, N) captured once into a CUDA graph, one parallel branch per
+        (function, N); a step replays it."""
+        torch = self.torch
+        for item in self.items:  # eager pass: sets kernel attributes outside capture
+            self._design_item(item)
+        torch.cuda.synchronize()
+        self.streams = [torch.cuda.Stream() for _ in self.items]
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            main = torch.cuda.current_stream()
+            for st, item in zip(self.streams, self.items):
+                st.wait_stream(main)
+                with torch.cuda.stream(st):
+                    self._design_item(item)
+            for st in self.streams:
+                main.wait_stream(st)
+        torch.cuda.synchronize()
+
+    def design_and_tables(self):
+        self.graph.replay()
 
     def step(self, events=None):
         self.design_and_tables()
@@ -380,10 +408,10 @@ def run_ours(args):
 
 
 def gpu_launches_per_step(wl) -> int:
-    # per (function, N): design 5 (setup + 4), projections 1+1 (interp: setup + 1;
-    # project: setup + 2 -> counted 2 + 3), two table rebuilds of 2 kernels,
-    # four evaluations
-    per_item = 5 + 2 + 3 + 4 + 4
+    # per (function, N): design 5 (descriptor setup + density, chunk scan,
+    # cumulative, inversion), interpolant values 2, projection 3, two table
+    # rebuilds of 3 kernels, four evaluations
+    per_item = 5 + 2 + 3 + 6 + 4
     return per_item * len(wl.items)
 
 
@@ -528,8 +556,84 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_launches(fn, reps: int = 5) -> float:
+    """Average device time of fn() in seconds (CUDA events, after one warm-up)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def run_variants(args):
+    """Per-table throughput of the evaluation paths (main cell-index path, the
+    paper's binary search, the texture filter) for the three functions and
+    N in {256, 1024, 4096}, and, at N = 1024, the error of FP32 / BF16 / FP16
+    vertex tables (max and RMS vs FP64 f and vs the FP64 CPWL)."""
+    import torch
+
+    import paper_1510_02975_gb300 as pwl
+    from paper_1510_02975_gb300 import _build
+    from paper_1510_02975_gb300 import workloads as W
+    _build.build()
+    m = 1 << args.log2m
+    y = torch.empty(m, dtype=torch.float32, device="cuda")
+    rows = []
+    errors = []
+    for name in FUNC_NAMES:
+        f = W.PAPER_FUNCTIONS[name]
+        xs = {"uniform": W.uniform_queries(f, m, seed=1), "normal": W.normal_queries(f, m, seed=2)}
+        for N in NS:
+            kn = pwl.pwl_design(f, N)
+            vp = pwl.pwl_project(f, kn, "project")
+            for dt in (("fp32", "bf16", "fp16") if N == 1024 else ("fp32",)):
+                t = pwl.Table(kn, vp, dt, args.k_cells)
+                for qs, x in xs.items():
+                    row = {"func": name, "N": N, "values": dt, "queries": qs, "K": int(t.info["k_cells"]),
+                           "n_chain": int(t.info["n_chain"]), "smem_kb": round(t.info["eval_smem_bytes"] / 1024, 1)}
+                    row["layout"] = int(t.info["layout"])
+                    for label, fn in (("main", lambda: pwl.pwl_eval(t.handle, x, y)),
+                                      ("cells8", lambda: pwl.pwl_eval_variant(t.handle, 2, x, y)),
+                                      ("cells16", lambda: pwl.pwl_eval_variant(t.handle, 3, x, y)),
+                                      ("search", lambda: pwl.pwl_eval_variant(t.handle, 0, x, y)),
+                                      ("texture", lambda: pwl.pwl_eval_variant(t.handle, 1, x, y))):
+                        if dt != "fp32" and label in ("search", "cells8", "cells16"):
+                            continue
+                        sec = time_launches(fn)
+                        row[label + "_gbs"] = round(BYTES_FWD * m / sec / 1e9, 1)
+                    rows.append(row)
+                if N == 1024:
+                    k64 = kn.cpu().numpy()
+                    v64 = vp.cpu().numpy()
+                    xd = xs["uniform"][: 1 << 20]
+                    xh = xd.cpu().numpy().astype(np.float64)
+                    for label, fn in (("fma", lambda: pwl.pwl_eval(t.handle, xd)),
+                                      ("texture", lambda: pwl.pwl_eval_variant(t.handle, 1, xd))):
+                        yv = fn().cpu().numpy().astype(np.float64)
+                        ef = yv - f64(name, xh)
+                        ep = yv - np.interp(xh, k64, v64)
+                        errors.append({"func": name, "N": N, "values": dt, "lerp": label,
+                                       "max_vs_f64_f": float(np.abs(ef).max()),
+                                       "rms_vs_f64_f": float(np.sqrt(np.mean(ef * ef))),
+                                       "max_vs_f64_pwl": float(np.abs(ep).max()),
+                                       "rms_vs_f64_pwl": float(np.sqrt(np.mean(ep * ep)))})
+                t.close()
+    peak, kind = measured_peaks()
+    print(json.dumps({"report": "variants", "queries_per_launch": m, "peak_gbs": peak, "peak_kind": kind,
+                      "throughput": rows, "errors": errors}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.report == "variants":
+        run_variants(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

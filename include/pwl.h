@@ -184,6 +184,8 @@ typedef struct {
     const void* d_values;  /* device, N+1 values in value_dtype */
     size_t eval_smem_bytes;     /* shared memory one forward CTA stages */
     size_t backward_smem_bytes; /* shared memory one backward CTA stages */
+    int32_t layout;             /* forward index pwl_eval uses: 0 = 8-byte, 1 = 16-byte records */
+    int32_t reserved2;
 } pwl_table_info;
 
 pwl_status pwl_table_get_info(pwl_table t, pwl_table_info* info);
@@ -207,7 +209,9 @@ pwl_status pwl_eval(pwl_table t, const void* d_x, void* d_y, int64_t m, int32_t 
  *   mode 1: the same interval search as pwl_eval, then the texture unit's
  *           linear filter at coordinate i - 1 + delta + 1/2 over the values
  *           (Section IV-B); the filter weight is fixed point (8 fractional
- *           bits), so results differ from pwl_eval by up to |v_i - v_{i-1}|/256.
+ *           bits), so results differ from pwl_eval by up to |v_i - v_{i-1}|/256;
+ *   mode 2, 3: pwl_eval forced to its 8-byte or 16-byte cell index (it
+ *           otherwise picks one per table, see pwl_table_info.layout).
  * x, y: device FP32 arrays of m elements.                                  */
 pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* d_y, int64_t m,
                             void* stream);

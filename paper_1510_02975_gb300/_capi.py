@@ -35,7 +35,8 @@ class PwlTableInfo(ctypes.Structure):
     _fields_ = [("n_intervals", ctypes.c_int64), ("k_cells", ctypes.c_int64), ("n_chain", ctypes.c_int64),
                 ("value_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32), ("a", ctypes.c_float),
                 ("b", ctypes.c_float), ("d_knots", ctypes.c_void_p), ("d_values", ctypes.c_void_p),
-                ("eval_smem_bytes", ctypes.c_size_t), ("backward_smem_bytes", ctypes.c_size_t)]
+                ("eval_smem_bytes", ctypes.c_size_t), ("backward_smem_bytes", ctypes.c_size_t),
+                ("layout", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p

@@ -38,24 +38,42 @@ struct BwdArgs {
     const float4* rec;  // backward records {x_j, j, s_j, s_{j+1} | link}
     const TableHeader* hdr;
     const float* inv_h;
+    const float* slope;
     int N, K, n_smem, max_chain;
     float a, b, inv_w, off;
+    float s_first, s_last;  // slopes of intervals 1 and N (set by the kernel)
     int64_t nvec;       // float4 vectors (x, gy and gx all 16-byte aligned), else 0
+};
+
+// Queries at or beyond the ends of [a, b] all feed the same four sums; a
+// skewed input (a query set clipped to the domain) can send half of them
+// there, so they are summed in registers and added once per thread at the
+// end instead of through contended shared-memory atomics.
+struct EndSums {
+    float clamped_left, clamped_right, at_a, at_b;
 };
 
 template <bool CHAINS>
 __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restrict__ srec,
                                          const float* __restrict__ s_ih, float* accA, float* accB,
-                                         const BwdArgs& p)
+                                         EndSums& e, const BwdArgs& p)
 {
     if (x != x) return x;  // NaN: no table contribution
-    if (x < p.a) {
-        atomicAdd(accA, g);
-        return 0.0f;
+    if (x <= p.a) {
+        if (x < p.a) {
+            e.clamped_left += g;
+            return 0.0f;
+        }
+        e.at_a += g;  // interval 1, delta = 0
+        return g * p.s_first;
     }
-    if (x > p.b) {
-        atomicAdd(accA + p.N + 1, g);
-        return 0.0f;
+    if (x >= p.b) {
+        if (x > p.b) {
+            e.clamped_right += g;
+            return 0.0f;
+        }
+        e.at_b += g;  // interval N, delta = 1
+        return g * p.s_last;
     }
     const int c = cell_of(x, p.inv_w, p.off, p.K);
     float4 r = (c < p.n_smem) ? srec[c] : __ldg(p.rec + c);
@@ -92,7 +110,7 @@ __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restr
 template <bool CHAINS>
 __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __restrict__ srec,
                                               const float* __restrict__ s_ih, float* accA, float* accB,
-                                              const float* x, const float* gy, float* gx, int64_t m)
+                                              EndSums& e, const float* x, const float* gy, float* gx, int64_t m)
 {
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -110,24 +128,24 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
 #pragma unroll
         for (int u = 0; u < kBwdUnroll; ++u) {
             float4 o;
-            o.x = bwd_one<CHAINS>(xs[u].x, gs[u].x, srec, s_ih, accA, accB, p);
-            o.y = bwd_one<CHAINS>(xs[u].y, gs[u].y, srec, s_ih, accA, accB, p);
-            o.z = bwd_one<CHAINS>(xs[u].z, gs[u].z, srec, s_ih, accA, accB, p);
-            o.w = bwd_one<CHAINS>(xs[u].w, gs[u].w, srec, s_ih, accA, accB, p);
+            o.x = bwd_one<CHAINS>(xs[u].x, gs[u].x, srec, s_ih, accA, accB, e, p);
+            o.y = bwd_one<CHAINS>(xs[u].y, gs[u].y, srec, s_ih, accA, accB, e, p);
+            o.z = bwd_one<CHAINS>(xs[u].z, gs[u].z, srec, s_ih, accA, accB, e, p);
+            o.w = bwd_one<CHAINS>(xs[u].w, gs[u].w, srec, s_ih, accA, accB, e, p);
             __stcs(ov + i + u * nthr, o);
         }
     }
     for (; i < p.nvec; i += nthr) {
         const float4 xs = __ldcs(xv + i), gs = __ldcs(gv + i);
         float4 o;
-        o.x = bwd_one<CHAINS>(xs.x, gs.x, srec, s_ih, accA, accB, p);
-        o.y = bwd_one<CHAINS>(xs.y, gs.y, srec, s_ih, accA, accB, p);
-        o.z = bwd_one<CHAINS>(xs.z, gs.z, srec, s_ih, accA, accB, p);
-        o.w = bwd_one<CHAINS>(xs.w, gs.w, srec, s_ih, accA, accB, p);
+        o.x = bwd_one<CHAINS>(xs.x, gs.x, srec, s_ih, accA, accB, e, p);
+        o.y = bwd_one<CHAINS>(xs.y, gs.y, srec, s_ih, accA, accB, e, p);
+        o.z = bwd_one<CHAINS>(xs.z, gs.z, srec, s_ih, accA, accB, e, p);
+        o.w = bwd_one<CHAINS>(xs.w, gs.w, srec, s_ih, accA, accB, e, p);
         __stcs(ov + i, o);
     }
     for (int64_t q = p.nvec * 4 + tid; q < m; q += nthr)
-        gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, p);
+        gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, e, p);
 }
 
 __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, const float* x, const float* gy,
@@ -139,9 +157,11 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     float* accA = s_ih + (args.N + 2);
     float* accB = accA + (args.N + 2);
     BwdArgs p = args;
-    const int n_chain = p.hdr->n_chain;
-    p.max_chain = p.hdr->max_chain;
+    const int n_chain = p.hdr->n_chain_b;
+    p.max_chain = p.hdr->max_chain_b;
     p.n_smem = min(p.K + n_chain, p.n_smem);
+    p.s_first = p.slope[1];
+    p.s_last = p.slope[p.N];
     for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) srec[i] = __ldg(p.rec + i);
     for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) {
         s_ih[i] = p.inv_h[i];
@@ -149,10 +169,23 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
         accB[i] = 0.0f;
     }
     __syncthreads();
+    EndSums e{0.0f, 0.0f, 0.0f, 0.0f};
     if (n_chain == 0)
-        backward_body<false>(p, srec, s_ih, accA, accB, x, gy, gx, m);
+        backward_body<false>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
     else
-        backward_body<true>(p, srec, s_ih, accA, accB, x, gy, gx, m);
+        backward_body<true>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
+    for (int o = 16; o > 0; o >>= 1) {
+        e.clamped_left += __shfl_xor_sync(0xffffffffu, e.clamped_left, o);
+        e.clamped_right += __shfl_xor_sync(0xffffffffu, e.clamped_right, o);
+        e.at_a += __shfl_xor_sync(0xffffffffu, e.at_a, o);
+        e.at_b += __shfl_xor_sync(0xffffffffu, e.at_b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(accA, e.clamped_left);
+        atomicAdd(accA + p.N + 1, e.clamped_right);
+        atomicAdd(accA + 1, e.at_a);
+        atomicAdd(accB + p.N, e.at_b);
+    }
     __syncthreads();
     float* row = partials + (size_t)blockIdx.x * 2 * (p.N + 2);
     for (int k = threadIdx.x; k < 2 * (p.N + 2); k += blockDim.x) row[k] = accA[k];
@@ -205,14 +238,15 @@ pwl_status backward_launch(pwl_table t, const float* x, const float* gy, float* 
     p.rec = t->rec_b;
     p.hdr = t->hdr;
     p.inv_h = t->inv_h;
+    p.slope = t->slope;
     p.N = (int)t->N;
-    p.K = (int)t->K;
+    p.K = (int)t->Kb;
     p.n_smem = (int)sh.n_smem;
     p.max_chain = 0;
     p.a = t->a;
     p.b = t->b;
-    p.inv_w = t->inv_w;
-    p.off = t->off;
+    p.inv_w = t->inv_w_b;
+    p.off = t->off_b;
     const uintptr_t ax = reinterpret_cast<uintptr_t>(x), ag = reinterpret_cast<uintptr_t>(gy),
                     ao = reinterpret_cast<uintptr_t>(gx);
     p.nvec = ((ax | ag | ao) % 16 == 0) ? m / 4 : 0;

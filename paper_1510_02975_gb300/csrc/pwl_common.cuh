@@ -132,17 +132,31 @@ pwl_status validate_func(const pwl_func* f);
 // ---------------------------------------------------------------------------
 // device table: FP32 knots, the uniform cell index and its records
 // ---------------------------------------------------------------------------
-// A record belongs to a knot j: {x_j, v_j, s_j, s_{j+1}} where s_j is the
-// slope of interval j = [x_{j-1}, x_j] (s_0 := s_1, s_{N+1} := s_N).  It gives
-// v exactly on [x_{j-1}, x_{j+1}]:  v(x) = v_j + (x - x_j) * (x < x_j ? s_j : s_{j+1}).
-// Cell c of the index holds the record of the first knot whose cell is c or,
-// if no knot falls in c, of the last knot before c.  When several knots share
-// a cell, the w field of a record is a link (a quiet NaN whose payload is the
-// index of the next knot's record in the chain area after the K cell
-// records) instead of s_{j+1}.  The backward records replace v_j by the
-// knot index j (as int bits).
+// Two cell indexes over [x_0, x_N] serve the kernels; both use uniform
+// cells and the cell function below.
+//
+// 8-byte index (K cells, forward path):
+//   - a cell no knot falls in lies inside one interval i; its record is that
+//     interval's line {y_c, s_i}, with y_c the line's value at the cell's
+//     anchor x_c = fma((float)c, w, a):  v(x) = y_c + (x - x_c) s_i;
+//   - a cell holding knot k (the first one, if several) has the record
+//     {tag(k), x_k}, tag = quiet NaN with payload k and a flag when more
+//     knots share the cell; the side record S[2k + (x >= x_k)] =
+//     {v_k, s_k} (left) or {v_k, s_{k+1}} (right) gives v(x) = v_k + (x - x_k) s.
+// 16-byte index (K_b cells, used by the backward and texture paths and by the
+// forward path for tables whose 8-byte index would not leave room for two
+// CTAs per SM): a record belongs to a knot j, {x_j, v_j, s_j, s_{j+1}}
+// (forward) or {x_j, j, s_j, s_{j+1}} (backward) with s_j the slope of
+// interval j (s_0 := s_1, s_{N+1} := s_N), so that
+// v(x) = v_j + (x - x_j) (x <= x_j ? s_j : s_{j+1}) on [x_{j-1}, x_{j+1}];
+// a cell holds the record of its first knot or, if no knot falls in it, of
+// the last knot before it; when several knots share a cell, the w field is a
+// link (quiet NaN whose payload indexes the next knot's record in the chain
+// area after the K_b cell records).
 constexpr uint32_t kLinkTag = 0x7FC00000u;
 constexpr uint32_t kLinkMask = 0x003FFFFFu;
+constexpr uint32_t kKnotTagMask = 0x001FFFFFu;  // knot index in a forward knot-cell tag
+constexpr uint32_t kKnotTagChain = 0x00200000u; // more knots share the cell
 
 __device__ __forceinline__ bool is_link(float w)
 {
@@ -150,6 +164,10 @@ __device__ __forceinline__ bool is_link(float w)
 }
 __device__ __forceinline__ int link_index(float w) { return (int)(__float_as_uint(w) & kLinkMask); }
 __device__ __forceinline__ float make_link(int j) { return __uint_as_float(kLinkTag | (uint32_t)j); }
+__device__ __forceinline__ float make_knot_tag(int k, bool chain)
+{
+    return __uint_as_float(kLinkTag | (chain ? kKnotTagChain : 0u) | (uint32_t)k);
+}
 
 // Cell of a point already clamped to [a, b]: c = trunc(x * inv_w + off)
 // with one rounding (fma), clamped to [0, K-1].  Monotone in x, which is
@@ -177,8 +195,11 @@ struct TableHeader {
     int32_t status;      // bit 0: knots not strictly increasing; bit 1: non-finite knot or value;
                          // bit 2: slope or reciprocal length not finite in FP32
     uint32_t hmin_bits;  // shortest interval (positive float, ordered as uint)
-    int32_t n_chain;     // chain records after the K cell records
-    int32_t max_chain;   // most chain hops any query can need
+    int32_t n_chain_b;   // backward index: chain records after the K_b cell records
+    int32_t max_chain_b; // backward index: most chain hops any query can need
+    int32_t n_chain_f;   // forward index: knots that share a cell with the previous knot
+    int32_t max_chain_f; // forward index: most extra knots in one cell
+    int32_t pad[2];
 };
 
 }  // namespace pwl
@@ -186,13 +207,20 @@ struct TableHeader {
 // The opaque handle behind pwl_table.
 struct pwl_table_s {
     int device;
-    int64_t N, K;
-    int64_t n_chain;        // chain records at the last synchronous build
-    int64_t chain_reserve;  // chain records the streaming kernels stage in shared memory
+    int64_t N;
     int32_t dtype;
-    float a, b, inv_w, off;
+    float a, b;
+    // forward index
+    int64_t K;
+    float inv_w, off, w;
+    int64_t n_chain_f;
+    // backward / texture index
+    int64_t Kb;
+    float inv_w_b, off_b;
+    int64_t n_chain_b;      // at the last synchronous build
+    int64_t chain_reserve_b;  // chain records the backward kernel stages in shared memory
     void* buf_base;    // header, knots, values, slopes, build scratch
-    void* buf_rec;     // forward + backward records
+    void* buf_rec;     // index records
     pwl::TableHeader* hdr;
     float* xk;
     float* vk;
@@ -201,8 +229,11 @@ struct pwl_table_s {
     void* vstore;      // N+1 values in dtype
     int* cj;           // build scratch: cell of every knot
     int* cpos;         // build scratch: chain slot of every knot
-    float4* rec_f;
-    float4* rec_b;
+    float2* recP;      // forward, 8-byte layout: K cell records
+    float2* recS;      // forward, 8-byte layout: 2 (N+1) side records
+    float4* rec16;     // forward, 16-byte layout on the K_b grid: K_b + N + 1 records
+    float4* rec_b;     // backward: K_b + N + 1 records
+    int32_t layout;    // forward layout pwl_eval uses: 0 = 8-byte cells, 1 = 16-byte cells
     cudaArray_t tex_array;
     cudaTextureObject_t tex;
 };

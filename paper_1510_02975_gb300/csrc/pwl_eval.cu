@@ -1,18 +1,26 @@
 // pwl_eval.cu -- CPWL evaluation (Algorithm 1) over a query stream.
 //
-// Main path (pwl_eval): a persistent grid; every CTA stages the table's cell
-// records in shared memory, then streams 16-byte vectors of queries with
-// several loads in flight per thread.  Per query: clamp to [x_0, x_N], one
-// fma + truncation for the cell (step 1 of Algorithm 1 reduced to a lookup),
-// one 16-byte shared-memory load of the record, a select between the two
-// slopes, and v_j + (x - x_j) * s (steps 2-3 fused into one FMA).  Cells
-// that hold several knots chain to further records (rare by construction).
+// Main path (pwl_eval): a persistent grid; every CTA stages a cell index
+// (8-byte cell records and the side records of the knots) in shared memory,
+// then streams 16-byte vectors of queries with several loads in flight per
+// thread.  Per query: clamp to [x_0, x_N]; one fma and a
+// truncation give the cell (step 1 of Algorithm 1 becomes a lookup); one
+// 8-byte shared-memory load gives the cell's line, y = y_c + (x - x_c) s
+// (steps 2-3 fused into one FMA).  Only queries whose cell holds a knot load
+// a second 8-byte side record, {v_k, s} for their side of the knot; several
+// knots in one cell (rare: the cells are narrower than most intervals) are
+// walked through the FP32 knot array.
+//
+// Tables whose 8-byte index would not leave room for two CTAs per SM use the
+// 16-byte index instead (one record {x_j, v_j, s_j, s_{j+1}} per cell, one
+// 16-byte load per query): fewer instructions, more shared-memory wavefronts.
 //
 // Comparison paths (pwl_eval_variant):
 //   mode 0  the paper's Algorithm 1: binary search over the FP32 knots in
 //           shared memory (Section IV), delta, (1 - delta) v_{i-1} + delta v_i
-//   mode 1  the same interval lookup as the main path, then the texture
-//           unit's linear filter at i - 1 + delta + 1/2 (Section IV-B).
+//   mode 1  interval lookup through the 16-byte index, then the texture
+//           unit's linear filter at i - 1 + delta + 1/2 (Section IV-B)
+//   mode 2, 3  the main path forced to the 8-byte or the 16-byte index.
 #include <math.h>
 
 #include <algorithm>
@@ -26,32 +34,77 @@ namespace {
 constexpr int kUnroll = 4;
 
 struct EvalArgs {
-    const float4* rec;
+    const float2* recP;   // 8-byte layout: K cell records
+    const float2* recS;   // 8-byte layout: 2 (N+1) side records
+    const float* xk;      // N+1 FP32 knots (chain walks of the 8-byte layout)
+    const float4* rec16;  // 16-byte layout: K cell records + chain area
     const TableHeader* hdr;
-    int K;
-    int n_smem;     // records staged in shared memory (at launch: the room reserved)
-    int max_chain;  // chain hops (set from the device header by the kernel)
-    float a, b, inv_w, off;
-    int64_t head;  // scalar queries before the first 16-byte boundary of x
-    int64_t nvec;  // 16-byte vectors after the head
+    int K, N;
+    int s_staged;         // 8-byte layout: side records in shared memory (else global)
+    int n_smem;           // 16-byte layout: records staged (at launch: the room reserved)
+    int max_chain;        // set from the device header by the kernel
+    float a, b, inv_w, off, w;
+    int64_t head;         // scalar queries before the first 16-byte boundary of x
+    int64_t nvec;         // 16-byte vectors after the head
 };
 
+// 8-byte layout.  Branch-free apart from chains: every lane computes its
+// cell anchor, knot lanes additionally load their side record (a predicated
+// load), and one FMA finishes.
 template <bool CHAINS>
-__device__ __forceinline__ float lerp_one(float x, const float4* __restrict__ srec, const EvalArgs& p)
-{
-    const float xc = clamp_nan(x, p.a, p.b);
-    const int c = cell_of(xc, p.inv_w, p.off, p.K);
-    float4 r = srec[c];
-    if (CHAINS) {
-        for (int g = 0; g < p.max_chain && xc > r.x && is_link(r.w); ++g) {
-            const int j = link_index(r.w);
-            r = (j < p.n_smem) ? srec[j] : __ldg(p.rec + j);
+struct Lerp8 {
+    const float2* sP;
+    const float2* sS;
+    const EvalArgs& p;
+    __device__ __forceinline__ float operator()(float x) const
+    {
+        const float xc = clamp_nan(x, p.a, p.b);
+        const int c = cell_of(xc, p.inv_w, p.off, p.K);
+        const float2 r = sP[c];
+        const uint32_t bits = __float_as_uint(r.x);
+        float anchor = __fmaf_rn(__int2float_rn(c), p.w, p.a);
+        float2 q = r;  // no knot in the cell: the cell's line {y_c, s} anchored at x_c
+        if ((bits & 0xFFC00000u) == kLinkTag) {
+            int k = (int)(bits & kKnotTagMask);
+            float xk = r.y;
+            if (CHAINS && (bits & kKnotTagChain)) {
+                for (int g = 0; g < p.max_chain && k < p.N; ++g) {
+                    const float xn = __ldg(p.xk + k + 1);
+                    if (!(xc >= xn)) break;
+                    ++k;
+                    xk = xn;
+                }
+            }
+            // x == x_k takes the right side: v_k + 0 * s is exactly v_k
+            const int si = 2 * k + (xc >= xk ? 1 : 0);
+            q = p.s_staged ? sS[si] : __ldg(p.recS + si);
+            anchor = xk;
         }
+        return __fmaf_rn(xc - anchor, q.y, q.x);
     }
-    // x == x_j takes the left slope: v_j + 0 * s_j is exactly v_j
-    const float s = (xc <= r.x) ? r.z : r.w;
-    return __fmaf_rn(xc - r.x, s, r.y);
-}
+};
+
+// 16-byte layout: one record {x_j, v_j, s_j, s_{j+1} | link} per cell.
+template <bool CHAINS>
+struct Lerp16 {
+    const float4* s16;
+    const EvalArgs& p;
+    __device__ __forceinline__ float operator()(float x) const
+    {
+        const float xc = clamp_nan(x, p.a, p.b);
+        const int c = cell_of(xc, p.inv_w, p.off, p.K);
+        float4 r = s16[c];
+        if (CHAINS) {
+            for (int g = 0; g < p.max_chain && xc > r.x && is_link(r.w); ++g) {
+                const int j = link_index(r.w);
+                r = (j < p.n_smem) ? s16[j] : __ldg(p.rec16 + j);
+            }
+        }
+        // x == x_j takes the left slope: v_j + 0 * s_j is exactly v_j
+        const float s = (xc <= r.x) ? r.z : r.w;
+        return __fmaf_rn(xc - r.x, s, r.y);
+    }
+};
 
 // 16-byte vectors of each I/O type
 template <typename IO>
@@ -60,13 +113,13 @@ template <>
 struct Vec<float> {
     static constexpr int n = 4;
     using T = float4;
-    template <bool C>
-    static __device__ __forceinline__ T apply(T v, const float4* s, const EvalArgs& p)
+    template <class L>
+    static __device__ __forceinline__ T apply(T v, const L& f)
     {
-        v.x = lerp_one<C>(v.x, s, p);
-        v.y = lerp_one<C>(v.y, s, p);
-        v.z = lerp_one<C>(v.z, s, p);
-        v.w = lerp_one<C>(v.w, s, p);
+        v.x = f(v.x);
+        v.y = f(v.y);
+        v.z = f(v.z);
+        v.w = f(v.w);
         return v;
     }
     static __device__ __forceinline__ float to_f(float x) { return x; }
@@ -76,16 +129,16 @@ template <>
 struct Vec<__nv_bfloat16> {
     static constexpr int n = 8;
     using T = uint4;
-    template <bool C>
-    static __device__ __forceinline__ T apply(T v, const float4* s, const EvalArgs& p)
+    template <class L>
+    static __device__ __forceinline__ T apply(T v, const L& f)
     {
         __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float2 f = __bfloat1622float2(h[k]);
-            f.x = lerp_one<C>(f.x, s, p);
-            f.y = lerp_one<C>(f.y, s, p);
-            h[k] = __float22bfloat162_rn(f);
+            float2 g = __bfloat1622float2(h[k]);
+            g.x = f(g.x);
+            g.y = f(g.y);
+            h[k] = __float22bfloat162_rn(g);
         }
         return v;
     }
@@ -96,16 +149,16 @@ template <>
 struct Vec<__half> {
     static constexpr int n = 8;
     using T = uint4;
-    template <bool C>
-    static __device__ __forceinline__ T apply(T v, const float4* s, const EvalArgs& p)
+    template <class L>
+    static __device__ __forceinline__ T apply(T v, const L& f)
     {
         __half2* h = reinterpret_cast<__half2*>(&v);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float2 f = __half22float2(h[k]);
-            f.x = lerp_one<C>(f.x, s, p);
-            f.y = lerp_one<C>(f.y, s, p);
-            h[k] = __float22half2_rn(f);
+            float2 g = __half22float2(h[k]);
+            g.x = f(g.x);
+            g.y = f(g.y);
+            h[k] = __float22half2_rn(g);
         }
         return v;
     }
@@ -119,9 +172,8 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
 __device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
 __device__ __forceinline__ void st_stream(uint4* p, uint4 v) { __stcs(p, v); }
 
-template <typename IO, bool CHAINS>
-__device__ __forceinline__ void eval_body(const EvalArgs& p, const float4* __restrict__ srec, const IO* x,
-                                          IO* y, int64_t m)
+template <typename IO, int U, class L>
+__device__ __forceinline__ void eval_body(const EvalArgs& p, const L& f, const IO* x, IO* y, int64_t m)
 {
     using V = Vec<IO>;
     using T = typename V::T;
@@ -130,37 +182,54 @@ __device__ __forceinline__ void eval_body(const EvalArgs& p, const float4* __res
     const T* xv = reinterpret_cast<const T*>(x + p.head);
     T* yv = reinterpret_cast<T*>(y + p.head);
     int64_t i = tid;
-    for (; i + (kUnroll - 1) * nthr < p.nvec; i += kUnroll * nthr) {
-        T v[kUnroll];
+    for (; i + (U - 1) * nthr < p.nvec; i += U * nthr) {
+        T v[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) v[u] = ld_stream(xv + i + u * nthr);
+        for (int u = 0; u < U; ++u) v[u] = ld_stream(xv + i + u * nthr);
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) v[u] = V::template apply<CHAINS>(v[u], srec, p);
+        for (int u = 0; u < U; ++u) v[u] = V::apply(v[u], f);
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) st_stream(yv + i + u * nthr, v[u]);
+        for (int u = 0; u < U; ++u) st_stream(yv + i + u * nthr, v[u]);
     }
-    for (; i < p.nvec; i += nthr) st_stream(yv + i, V::template apply<CHAINS>(ld_stream(xv + i), srec, p));
-    for (int64_t j = tid; j < p.head; j += nthr) y[j] = V::from_f(lerp_one<CHAINS>(V::to_f(x[j]), srec, p));
-    for (int64_t j = p.head + p.nvec * V::n + tid; j < m; j += nthr)
-        y[j] = V::from_f(lerp_one<CHAINS>(V::to_f(x[j]), srec, p));
+    for (; i < p.nvec; i += nthr) st_stream(yv + i, V::apply(ld_stream(xv + i), f));
+    for (int64_t j = tid; j < p.head; j += nthr) y[j] = V::from_f(f(V::to_f(x[j])));
+    for (int64_t j = p.head + p.nvec * V::n + tid; j < m; j += nthr) y[j] = V::from_f(f(V::to_f(x[j])));
 }
 
-// MINB = 2 asks for <= 32 registers so that two 1024-thread CTAs fit an SM
-// (used when two copies of the records fit its shared memory).
-template <typename IO, int MINB>
+// LAYOUT 0: 8-byte index; 1: 16-byte index.  MINB = 2 asks for <= 32
+// registers so that two 1024-thread CTAs fit an SM (used when two copies of
+// the index fit its shared memory); it keeps two 16-byte vectors in flight
+// per thread instead of four, the same bytes in flight per SM.
+template <typename IO, int LAYOUT, int MINB>
 __global__ void __launch_bounds__(1024, MINB) eval_kernel(const EvalArgs args, const IO* x, IO* y, int64_t m)
 {
-    extern __shared__ float4 srec[];
+    constexpr int U = (MINB >= 2) ? kUnroll / 2 : kUnroll;
+    extern __shared__ float4 s_fwd[];
     EvalArgs p = args;
-    const int n_chain = p.hdr->n_chain;
-    p.max_chain = p.hdr->max_chain;
-    p.n_smem = min(p.K + n_chain, p.n_smem);  // the rest of the chain area stays in global memory
-    for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) srec[i] = __ldg(p.rec + i);
-    __syncthreads();
-    if (n_chain == 0)
-        eval_body<IO, false>(p, srec, x, y, m);
-    else
-        eval_body<IO, true>(p, srec, x, y, m);
+    if (LAYOUT == 0) {
+        float2* sP = reinterpret_cast<float2*>(s_fwd);
+        float2* sS = sP + p.K;
+        const int n_chain = p.hdr->n_chain_f;
+        p.max_chain = p.hdr->max_chain_f;
+        for (int i = threadIdx.x; i < p.K; i += blockDim.x) sP[i] = __ldg(p.recP + i);
+        if (p.s_staged)
+            for (int i = threadIdx.x; i < 2 * (p.N + 1); i += blockDim.x) sS[i] = __ldg(p.recS + i);
+        __syncthreads();
+        if (n_chain == 0)
+            eval_body<IO, U>(p, Lerp8<false>{sP, sS, p}, x, y, m);
+        else
+            eval_body<IO, U>(p, Lerp8<true>{sP, sS, p}, x, y, m);
+    } else {
+        const int n_chain = p.hdr->n_chain_b;
+        p.max_chain = p.hdr->max_chain_b;
+        p.n_smem = min(p.K + n_chain, p.n_smem);  // the rest of the chain area stays in global memory
+        for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) s_fwd[i] = __ldg(p.rec16 + i);
+        __syncthreads();
+        if (n_chain == 0)
+            eval_body<IO, U>(p, Lerp16<false>{s_fwd, p}, x, y, m);
+        else
+            eval_body<IO, U>(p, Lerp16<true>{s_fwd, p}, x, y, m);
+    }
 }
 
 // ---- mode 0: Algorithm 1 with a binary search over the knots --------------
@@ -189,36 +258,42 @@ __global__ void __launch_bounds__(1024) eval_search_kernel(const float* __restri
 }
 
 // ---- mode 1: interval lookup, then the texture unit's linear filter -------
-__global__ void __launch_bounds__(1024) eval_tex_kernel(const EvalArgs args, const float* __restrict__ inv_h_g,
-                                                        int N, cudaTextureObject_t tex, const float* x,
+struct TexArgs {
+    const float4* rec;  // backward records
+    const TableHeader* hdr;
+    const float* inv_h;
+    int K, N, n_smem;
+    float a, b, inv_w, off;
+};
+
+__global__ void __launch_bounds__(1024) eval_tex_kernel(const TexArgs p, cudaTextureObject_t tex, const float* x,
                                                         float* y, int64_t m)
 {
     extern __shared__ float4 s_dyn[];
-    float4* srec = s_dyn;                                          // backward-form records
-    float* s_ih = reinterpret_cast<float*>(s_dyn + args.n_smem);   // N+2 reciprocal lengths
-    EvalArgs p = args;
-    p.max_chain = p.hdr->max_chain;
-    p.n_smem = min(p.K + p.hdr->n_chain, p.n_smem);
-    for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) srec[i] = __ldg(p.rec + i);
-    for (int i = threadIdx.x; i < N + 2; i += blockDim.x) s_ih[i] = inv_h_g[i];
+    float4* srec = s_dyn;                                        // backward-form records
+    float* s_ih = reinterpret_cast<float*>(s_dyn + p.n_smem);    // N+2 reciprocal lengths
+    const int max_chain = p.hdr->max_chain_b;
+    const int n_stage = min(p.K + p.hdr->n_chain_b, p.n_smem);
+    for (int i = threadIdx.x; i < n_stage; i += blockDim.x) srec[i] = __ldg(p.rec + i);
+    for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) s_ih[i] = p.inv_h[i];
     __syncthreads();
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += nthr) {
         const float xc = clamp_nan(__ldcs(x + q), p.a, p.b);
         const int c = cell_of(xc, p.inv_w, p.off, p.K);
-        float4 r = (c < p.n_smem) ? srec[c] : __ldg(p.rec + c);
-        for (int g = 0; g < p.max_chain && xc >= r.x && is_link(r.w); ++g) {
+        float4 r = (c < n_stage) ? srec[c] : __ldg(p.rec + c);
+        for (int g = 0; g < max_chain && xc >= r.x && is_link(r.w); ++g) {
             const int j = link_index(r.w);
-            r = (j < p.n_smem) ? srec[j] : __ldg(p.rec + j);
+            r = (j < n_stage) ? srec[j] : __ldg(p.rec + j);
         }
         const int j = __float_as_int(r.y);
         float u;  // texel coordinate i - 1 + delta + 1/2
         if (xc < r.x) {
             u = (float)j + 0.5f - (r.x - xc) * s_ih[j];
-        } else if (j < N) {
+        } else if (j < p.N) {
             u = (float)j + 0.5f + (xc - r.x) * s_ih[j + 1];
         } else {
-            u = (float)N + 0.5f;
+            u = (float)p.N + 0.5f;
         }
         float yv = tex1D<float>(tex, u);
         if (xc != xc) yv = xc;
@@ -238,27 +313,34 @@ pwl_status check_common(pwl_table t, const void* x, const void* y, int64_t m)
     return PWL_OK;
 }
 
-EvalArgs make_args(pwl_table t, const float4* rec, int64_t n_smem)
+template <typename IO>
+pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, cudaStream_t s)
 {
     EvalArgs p{};
-    p.rec = rec;
+    p.recP = t->recP;
+    p.recS = t->recS;
+    p.xk = t->xk;
+    p.rec16 = t->rec16;
     p.hdr = t->hdr;
-    p.K = (int)t->K;
-    p.n_smem = (int)n_smem;
-    p.max_chain = 0;
+    p.N = (int)t->N;
     p.a = t->a;
     p.b = t->b;
-    p.inv_w = t->inv_w;
-    p.off = t->off;
-    return p;
-}
-
-template <typename IO>
-pwl_status launch_eval(pwl_table t, const IO* x, IO* y, int64_t m, cudaStream_t s)
-{
-    const int64_t n_smem = eval_smem_records(t);
-    if (n_smem < t->K) return fail(PWL_ENOTSUP, "cell index of %lld records does not fit one CTA", (long long)t->K);
-    EvalArgs p = make_args(t, t->rec_f, n_smem);
+    size_t smem;
+    if (layout == 0) {
+        p.K = (int)t->K;
+        p.s_staged = forward_side_staged(t->N) ? 1 : 0;
+        p.inv_w = t->inv_w;
+        p.off = t->off;
+        p.w = t->w;
+        smem = eval8_smem_bytes(t);
+    } else {
+        p.K = (int)t->Kb;
+        p.n_smem = (int)eval16_smem_records(t);
+        p.inv_w = t->inv_w_b;
+        p.off = t->off_b;
+        smem = eval16_smem_bytes(t);
+        if (p.n_smem < p.K) return fail(PWL_ENOTSUP, "16-byte index of %d cells does not fit one CTA", p.K);
+    }
     const uintptr_t ax = reinterpret_cast<uintptr_t>(x), ay = reinterpret_cast<uintptr_t>(y);
     if ((ax % 16) == (ay % 16) && (ax % sizeof(IO)) == 0) {
         const int64_t head = std::min<int64_t>(m, (int64_t)(((16 - ax % 16) % 16) / sizeof(IO)));
@@ -268,14 +350,18 @@ pwl_status launch_eval(pwl_table t, const IO* x, IO* y, int64_t m, cudaStream_t 
         p.head = 0;
         p.nvec = 0;
     }
-    const size_t smem = sizeof(float4) * (size_t)n_smem;
     const DeviceInfo& di = device_info();
+    if (smem > di.smem_optin) return fail(PWL_ENOTSUP, "forward index of %zu bytes does not fit one CTA", smem);
     const bool two = di.smem_per_sm >= 2 * (smem + 1024);
-    auto kern = two ? eval_kernel<IO, 2> : eval_kernel<IO, 1>;
+    void (*kern)(const EvalArgs, const IO*, IO*, int64_t);
+    if (layout == 0)
+        kern = two ? eval_kernel<IO, 0, 2> : eval_kernel<IO, 0, 1>;
+    else
+        kern = two ? eval_kernel<IO, 1, 2> : eval_kernel<IO, 1, 1>;
     int max_grid = 0;
     PWL_CUDA_TRY(occupancy_grid(kern, 1024, smem, &max_grid));
     // no more CTAs than there are unrolled vector groups (small launches
-    // should not stage the table in hundreds of idle CTAs)
+    // should not stage the index in hundreds of idle CTAs)
     const int64_t units = p.nvec + (m - p.nvec * Vec<IO>::n);
     const int64_t per_cta = (int64_t)1024 * kUnroll;
     const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, (units + per_cta - 1) / per_cta));
@@ -287,8 +373,6 @@ pwl_status launch_eval(pwl_table t, const IO* x, IO* y, int64_t m, cudaStream_t 
 pwl_status ensure_texture(pwl_table t)
 {
     if (t->tex) return PWL_OK;
-    int maxw = 0;
-    cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, t->device);
     int maxa = 0;
     cudaDeviceGetAttribute(&maxa, cudaDevAttrMaxTexture1DWidth, t->device);
     if (t->N + 1 > maxa)
@@ -329,12 +413,12 @@ pwl_status pwl_eval(pwl_table t, const void* d_x, void* d_y, int64_t m, int32_t 
     cudaStream_t s = as_stream(stream);
     switch (io_dtype) {
     case PWL_FP32:
-        return launch_eval<float>(t, static_cast<const float*>(d_x), static_cast<float*>(d_y), m, s);
+        return launch_eval<float>(t, t->layout, static_cast<const float*>(d_x), static_cast<float*>(d_y), m, s);
     case PWL_BF16:
-        return launch_eval<__nv_bfloat16>(t, static_cast<const __nv_bfloat16*>(d_x),
+        return launch_eval<__nv_bfloat16>(t, t->layout, static_cast<const __nv_bfloat16*>(d_x),
                                           static_cast<__nv_bfloat16*>(d_y), m, s);
     case PWL_FP16:
-        return launch_eval<__half>(t, static_cast<const __half*>(d_x), static_cast<__half*>(d_y), m, s);
+        return launch_eval<__half>(t, t->layout, static_cast<const __half*>(d_x), static_cast<__half*>(d_y), m, s);
     }
     return fail(PWL_EINVAL, "unknown io dtype %d", io_dtype);
 }
@@ -345,10 +429,11 @@ pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* 
     clear_error();
     pwl_status st = check_common(t, d_x, d_y, m);
     if (st != PWL_OK) return st;
-    if (mode != 0 && mode != 1) return fail(PWL_EINVAL, "unknown mode %d", mode);
+    if (mode < 0 || mode > 3) return fail(PWL_EINVAL, "unknown mode %d", mode);
     if (m == 0) return PWL_OK;
     cudaStream_t s = as_stream(stream);
     const DeviceInfo& di = device_info();
+    if (mode >= 2) return launch_eval<float>(t, mode - 2, d_x, d_y, m, s);
     if (mode == 0) {
         const size_t smem = sizeof(float2) * (size_t)(t->N + 1);
         if (smem > di.smem_optin)
@@ -363,12 +448,21 @@ pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* 
     if (st != PWL_OK) return st;
     const size_t fixed = sizeof(float) * (size_t)(t->N + 2);
     if (fixed + 1024 > di.smem_optin) return fail(PWL_ENOTSUP, "table too large for the texture path");
-    const int64_t n_smem = std::min<int64_t>(t->K + t->chain_reserve, (int64_t)((di.smem_optin - fixed) / 16));
-    EvalArgs p = make_args(t, t->rec_b, n_smem);
-    const size_t smem = 16 * (size_t)n_smem + fixed;
+    TexArgs p{};
+    p.rec = t->rec_b;
+    p.hdr = t->hdr;
+    p.inv_h = t->inv_h;
+    p.K = (int)t->Kb;
+    p.N = (int)t->N;
+    p.n_smem = (int)std::min<int64_t>(t->Kb + t->chain_reserve_b, (int64_t)((di.smem_optin - fixed) / 16));
+    p.a = t->a;
+    p.b = t->b;
+    p.inv_w = t->inv_w_b;
+    p.off = t->off_b;
+    const size_t smem = 16 * (size_t)p.n_smem + fixed;
     int grid = 0;
     PWL_CUDA_TRY(occupancy_grid(eval_tex_kernel, 1024, smem, &grid));
-    eval_tex_kernel<<<grid, 1024, smem, s>>>(p, t->inv_h, (int)t->N, t->tex, d_x, d_y, m);
+    eval_tex_kernel<<<grid, 1024, smem, s>>>(p, t->tex, d_x, d_y, m);
     PWL_CHECK_LAUNCH("eval_tex_kernel");
     return PWL_OK;
 }

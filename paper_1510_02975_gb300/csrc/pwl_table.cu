@@ -1,14 +1,17 @@
 // pwl_table.cu -- device representation of a CPWL function: the inputs of
 // Algorithm 1 (knots x_samples and values v_samples) rounded to their storage
-// types, plus a uniform cell index over [x_0, x_N] whose records make the
-// search step of Algorithm 1 a single lookup.
+// types, plus uniform cell indexes over [x_0, x_N] whose records make the
+// search step of Algorithm 1 a single lookup (see pwl_common.cuh).
 //
-// Build = two single-CTA kernels separated by one host synchronisation:
-//   table_round_kernel  FP64 -> FP32 knots, values -> dtype (-> FP32), slopes,
-//                       reciprocal lengths, validation and the shortest interval
-//   table_index_kernel  cell of every knot, chain positions, cell records
-// The host picks the cell count K between the two from the shortest
-// interval (cells no wider than it hold at most one knot).
+// Build (all single-CTA kernels, one host synchronisation in between):
+//   table_round_kernel    FP64 -> FP32 knots, values -> dtype (-> FP32),
+//                         slopes, reciprocal lengths, validation, shortest
+//                         interval
+//   table_index_b_kernel  backward index: cell of every knot, chain slots,
+//                         16-byte knot records
+//   table_index_f_kernel  forward index: 8-byte cell records, side records
+// The host picks both cell counts between the first kernel and the others
+// from the shortest interval and the shared-memory budgets.
 #include <math.h>
 #include <string.h>
 
@@ -22,7 +25,6 @@ namespace pwl {
 namespace {
 
 constexpr int kBuildThreads = 1024;
-
 
 __device__ __forceinline__ int block_exclusive_scan_int(int v, int* s_warp, int* total)
 {
@@ -110,10 +112,10 @@ __global__ void __launch_bounds__(kBuildThreads) table_round_kernel(
     else atomicMin(&s_hmin, 0u);
     __syncthreads();
     if (threadIdx.x == 0) {
-        hdr->status = s_status;
-        hdr->hmin_bits = s_hmin;
-        hdr->n_chain = 0;
-        hdr->max_chain = 0;
+        TableHeader h{};
+        h.status = s_status;
+        h.hmin_bits = s_hmin;
+        *hdr = h;
     }
 }
 
@@ -128,16 +130,28 @@ __device__ __forceinline__ int lower_bound_int(const int* c, int n, int v)
     return lo;
 }
 
-__global__ void __launch_bounds__(kBuildThreads) table_index_kernel(
+// Cells of all knots, and the largest number of extra knots in one cell.
+__device__ void knot_cells(int N, int K, float inv_w, float off, const float* __restrict__ xk, int* cj,
+                           int* s_maxchain)
+{
+    for (int j = threadIdx.x; j <= N; j += blockDim.x) cj[j] = cell_of(xk[j], inv_w, off, K);
+    __syncthreads();
+    int my_max = 0;
+    for (int j = 1 + threadIdx.x; j <= N; j += blockDim.x)
+        if (cj[j] == cj[j - 1]) my_max = max(my_max, j - lower_bound_int(cj, N + 1, cj[j]));
+    if (my_max) atomicMax(s_maxchain, my_max);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBuildThreads) table_index_b_kernel(
     int N, int K, float inv_w, float off, const float* __restrict__ xk, const float* __restrict__ vk,
-    const float* __restrict__ slope, int* cj, int* cpos, float4* rec_f, float4* rec_b,
-    TableHeader* hdr)
+    const float* __restrict__ slope, int* cj, int* cpos, float4* rec16, float4* rec_b, TableHeader* hdr)
 {
     __shared__ int s_warp[33];
     __shared__ int s_maxchain;
     if (threadIdx.x == 0) s_maxchain = 0;
-    for (int j = threadIdx.x; j <= N; j += blockDim.x) cj[j] = cell_of(xk[j], inv_w, off, K);
     __syncthreads();
+    knot_cells(N, K, inv_w, off, xk, cj, &s_maxchain);
     int carry = 0;
     for (int base = 0; base <= N; base += blockDim.x) {
         const int j = base + threadIdx.x;
@@ -149,7 +163,6 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_kernel(
     }
     const int n_chain = carry;
     __syncthreads();
-    // records of the K cells
     for (int c = threadIdx.x; c < K; c += blockDim.x) {
         const int lb = lower_bound_int(cj, N + 1, c);
         int j;
@@ -161,50 +174,65 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_kernel(
             j = lb - 1;
         }
         const float w = chained ? make_link(K + cpos[j + 1]) : slope[j + 1];
-        rec_f[c] = make_float4(xk[j], vk[j], slope[j], w);
+        rec16[c] = make_float4(xk[j], vk[j], slope[j], w);
         rec_b[c] = make_float4(xk[j], __int_as_float(j), slope[j], w);
     }
-    // chain records: knots that share their cell with the previous knot
-    int my_max = 0;
     for (int j = 1 + threadIdx.x; j <= N; j += blockDim.x) {
         if (cj[j] != cj[j - 1]) continue;
         const bool chained = (j < N && cj[j + 1] == cj[j]);
         const float w = chained ? make_link(K + cpos[j + 1]) : slope[j + 1];
-        const int idx = K + cpos[j];
-        rec_f[idx] = make_float4(xk[j], vk[j], slope[j], w);
-        rec_b[idx] = make_float4(xk[j], __int_as_float(j), slope[j], w);
-        my_max = max(my_max, j - lower_bound_int(cj, N + 1, cj[j]));
+        rec16[K + cpos[j]] = make_float4(xk[j], vk[j], slope[j], w);
+        rec_b[K + cpos[j]] = make_float4(xk[j], __int_as_float(j), slope[j], w);
     }
-    if (my_max) atomicMax(&s_maxchain, my_max);
+    if (threadIdx.x == 0) {
+        hdr->n_chain_b = n_chain;
+        hdr->max_chain_b = s_maxchain;
+    }
+}
+
+__global__ void __launch_bounds__(kBuildThreads) table_index_f_kernel(
+    int N, int K, float inv_w, float off, float w, float a, const float* __restrict__ xk,
+    const float* __restrict__ vk, const float* __restrict__ slope, int* cj, float2* recP, float2* recS,
+    TableHeader* hdr)
+{
+    __shared__ int s_maxchain;
+    __shared__ int s_nchain;
+    if (threadIdx.x == 0) {
+        s_maxchain = 0;
+        s_nchain = 0;
+    }
+    __syncthreads();
+    knot_cells(N, K, inv_w, off, xk, cj, &s_maxchain);
+    int my_chain = 0;
+    for (int j = 1 + threadIdx.x; j <= N; j += blockDim.x) my_chain += (cj[j] == cj[j - 1]) ? 1 : 0;
+    if (my_chain) atomicAdd(&s_nchain, my_chain);
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        const int lb = lower_bound_int(cj, N + 1, c);
+        if (lb <= N && cj[lb] == c) {
+            const bool chain = (lb < N && cj[lb + 1] == c);
+            recP[c] = make_float2(make_knot_tag(lb, chain), xk[lb]);
+        } else {
+            // the line of interval j+1 through (x_j, v_j), valued at the anchor x_c
+            const int j = lb - 1;
+            const float xc = __fmaf_rn(__int2float_rn(c), w, a);
+            const double s = ((double)vk[j + 1] - (double)vk[j]) / ((double)xk[j + 1] - (double)xk[j]);
+            const double yc = (double)vk[j] + ((double)xc - (double)xk[j]) * s;
+            recP[c] = make_float2(__double2float_rn(yc), slope[j + 1]);
+        }
+    }
+    for (int k = threadIdx.x; k <= N; k += blockDim.x) {
+        recS[2 * k] = make_float2(vk[k], slope[k]);
+        recS[2 * k + 1] = make_float2(vk[k], slope[k + 1]);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        hdr->n_chain = n_chain;
-        hdr->max_chain = s_maxchain;
+        hdr->n_chain_f = s_nchain;
+        hdr->max_chain_f = s_maxchain;
     }
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-}  // namespace
-
-int64_t choose_cells(int64_t N, float a, float b, float hmin, int64_t requested)
-{
-    const DeviceInfo& di = device_info();
-    const int64_t link_cap = (int64_t)kLinkMask - N - 2;
-    // as many records as one CTA can stage next to nothing else (forward
-    // kernel), leaving 8 KB for the chain records of the cells that overflow;
-    // the forward kernel relies on every cell record being staged
-    const int64_t cap = std::min<int64_t>((int64_t)((di.smem_optin - 8192) / sizeof(float4)), link_cap);
-    if (requested > 0) return std::min<int64_t>(requested, cap);
-    // cells no wider than the shortest interval: at most one knot per cell
-    const double need = ceil(((double)b - (double)a) / (double)hmin) + 1.0;
-    int64_t K = (int64_t)std::min<double>(need, (double)cap);
-    return std::max<int64_t>(K, 1);
-}
-
-namespace {
-
-// Launches both build kernels for a table whose buffers and K are set.
 pwl_status launch_build(pwl_table t, const double* d_knots, const double* d_values, bool index_only,
                         cudaStream_t s)
 {
@@ -214,9 +242,12 @@ pwl_status launch_build(pwl_table t, const double* d_knots, const double* d_valu
                                                        t->slope, t->inv_h, t->hdr);
         PWL_CHECK_LAUNCH("table_round_kernel");
     }
-    table_index_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->K, t->inv_w, t->off, t->xk, t->vk, t->slope,
-                                                   t->cj, t->cpos, t->rec_f, t->rec_b, t->hdr);
-    PWL_CHECK_LAUNCH("table_index_kernel");
+    table_index_b_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->Kb, t->inv_w_b, t->off_b, t->xk, t->vk, t->slope,
+                                                     t->cj, t->cpos, t->rec16, t->rec_b, t->hdr);
+    PWL_CHECK_LAUNCH("table_index_b_kernel");
+    table_index_f_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->K, t->inv_w, t->off, t->w, t->a, t->xk, t->vk,
+                                                     t->slope, t->cj, t->recP, t->recS, t->hdr);
+    PWL_CHECK_LAUNCH("table_index_f_kernel");
     return PWL_OK;
 }
 
@@ -229,6 +260,61 @@ pwl_status status_error(const TableHeader& h)
 }
 
 }  // namespace
+
+int64_t forward_cell_capacity(int64_t N, size_t budget)
+{
+    const size_t side = forward_side_bytes(N);
+    const size_t fixed = forward_side_staged(N) ? side : 0;
+    if (fixed + 8 * 64 > budget) return 64;
+    return (int64_t)((budget - fixed) / sizeof(float2));
+}
+
+int64_t backward_cell_capacity(int64_t N)
+{
+    const size_t optin = device_info().smem_optin;
+    const size_t fixed = 12 * (size_t)(N + 2) + 8 * 1024;  // reciprocal lengths, accumulators, chains
+    if (fixed + 16 * 64 > optin) return (int64_t)((optin - 8 * 1024) / sizeof(float4));
+    return (int64_t)((optin - fixed) / sizeof(float4));
+}
+
+void choose_cells(pwl_table t, float hmin, int64_t requested)
+{
+    const DeviceInfo& di = device_info();
+    const int64_t N = t->N;
+    // cells no wider than the shortest interval hold at most one knot
+    const double need = ceil(((double)t->b - (double)t->a) / (double)hmin) + 1.0;
+    // 8-byte index: worth its second, dependent gather on knot cells only
+    // when it lets two CTAs share an SM while most cells (>= 3/4) are
+    // knot-free; otherwise the 16-byte index serves the forward path too
+    const size_t half = di.smem_per_sm / 2 - 1024;
+    const int64_t cap2 = forward_cell_capacity(N, half);
+    const int64_t cap1 = forward_cell_capacity(N, di.smem_optin);
+    const double want = std::max<double>(need, 8.0 * (double)(N + 1));
+    int64_t K;
+    if (requested > 0) {
+        K = std::min<int64_t>(requested, cap1);
+        t->layout = (K <= cap2 && K >= 4 * (N + 1)) ? 0 : 1;
+    } else if (cap2 >= 4 * (N + 1)) {
+        K = (int64_t)std::min<double>(want, (double)cap2);
+        t->layout = 0;
+    } else {
+        K = (int64_t)std::min<double>(want, (double)cap1);
+        t->layout = 1;
+    }
+    t->K = std::max<int64_t>(K, 1);
+    const int64_t capb = backward_cell_capacity(N);
+    int64_t Kb = (requested > 0) ? std::min<int64_t>(requested, capb)
+                                 : (int64_t)std::min<double>(std::max<double>(need, 2.0 * (double)(N + 1)),
+                                                              (double)capb);
+    t->Kb = std::max<int64_t>(std::min<int64_t>(Kb, (int64_t)kLinkMask - N - 2), 1);
+    // cell functions c = trunc(fma(x, inv_w, off)), inv_w = K / (b - a);
+    // 8-byte-index anchors x_c = fma(c, w, a), w = (b - a) / K
+    t->inv_w = (float)t->K / (t->b - t->a);
+    t->off = -t->a * t->inv_w;
+    t->w = (t->b - t->a) / (float)t->K;
+    t->inv_w_b = (float)t->Kb / (t->b - t->a);
+    t->off_b = -t->a * t->inv_w_b;
+}
 
 }  // namespace pwl
 
@@ -303,23 +389,29 @@ pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_
     memcpy(&hmin, &h.hmin_bits, 4);
     t->a = ab[0];
     t->b = ab[1];
-    t->K = choose_cells(N, t->a, t->b, hmin, k_cells);
-    // the cell function: c = trunc(fma(x, inv_w, off)), inv_w = K / (b - a)
-    t->inv_w = (float)t->K / (t->b - t->a);
-    t->off = -t->a * t->inv_w;
-    const size_t nrec = (size_t)t->K + n1;
-    if ((e = cudaMalloc(&t->buf_rec, 2 * align256(sizeof(float4) * nrec))) != cudaSuccess)
+    choose_cells(t, hmin, k_cells);
+    const size_t bytes_b = align256(sizeof(float4) * ((size_t)t->Kb + n1));
+    const size_t bytes_p = align256(sizeof(float2) * (size_t)t->K);
+    const size_t bytes_s = align256(sizeof(float2) * 2 * n1);
+    if ((e = cudaMalloc(&t->buf_rec, 2 * bytes_b + bytes_p + bytes_s)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMalloc(records)"));
-    t->rec_f = static_cast<float4*>(t->buf_rec);
-    t->rec_b = reinterpret_cast<float4*>(static_cast<char*>(t->buf_rec) + align256(sizeof(float4) * nrec));
+    char* r = static_cast<char*>(t->buf_rec);
+    t->rec_b = reinterpret_cast<float4*>(r);
+    t->rec16 = reinterpret_cast<float4*>(r + bytes_b);
+    t->recP = reinterpret_cast<float2*>(r + 2 * bytes_b);
+    t->recS = reinterpret_cast<float2*>(r + 2 * bytes_b + bytes_p);
     if ((st = launch_build(t, d_knots, d_values, true, s)) != PWL_OK) return bail(st);
     if ((e = cudaMemcpyAsync(&h, t->hdr, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return bail(cuda_fail(e, "table build (index pass)"));
-    t->n_chain = h.n_chain;
+    t->n_chain_b = h.n_chain_b;
+    t->n_chain_f = h.n_chain_f;
+    // chains in the 16-byte index (cells holding several knots) cost more than
+    // the 8-byte index's single-CTA occupancy when the latter has none
+    if (t->layout == 1 && k_cells == 0 && t->n_chain_b > 0 && t->n_chain_f == 0) t->layout = 0;
     // shared-memory room for the chains of this build and of later updates
     // that move a few knots (further chain records are read from global memory)
-    t->chain_reserve = std::min<int64_t>((int64_t)n1, t->n_chain + 64);
+    t->chain_reserve_b = std::min<int64_t>((int64_t)n1, t->n_chain_b + 64);
     *out = t;
     return PWL_OK;
 }
@@ -364,13 +456,14 @@ pwl_status pwl_table_get_info(pwl_table t, pwl_table_info* info)
     memset(info, 0, sizeof(*info));
     info->n_intervals = t->N;
     info->k_cells = t->K;
-    info->n_chain = t->n_chain;
+    info->n_chain = t->n_chain_f;
     info->value_dtype = t->dtype;
     info->a = t->a;
     info->b = t->b;
     info->d_knots = t->xk;
     info->d_values = t->vstore;
-    info->eval_smem_bytes = eval_smem_bytes(t);
+    info->eval_smem_bytes = t->layout == 0 ? eval8_smem_bytes(t) : eval16_smem_bytes(t);
+    info->layout = t->layout;
     info->backward_smem_bytes = backward_smem_bytes(t);
     return PWL_OK;
 }

@@ -8,18 +8,34 @@
 
 namespace pwl {
 
-int64_t choose_cells(int64_t N, float a, float b, float hmin, int64_t requested);
-
-// Records (cells + reserved chain area) the forward kernel can stage in
-// shared memory; chain records beyond the reserve are read from global memory.
-inline int64_t eval_smem_records(const pwl_table_s* t)
+// Forward index: K 8-byte cell records plus 2 (N+1) 8-byte side records.
+inline size_t forward_side_bytes(int64_t N) { return sizeof(float2) * 2 * (size_t)(N + 1); }
+// The side records are staged in shared memory when they leave room for at
+// least 1024 cell records; otherwise the kernel reads them from global memory.
+inline bool forward_side_staged(int64_t N)
+{
+    return forward_side_bytes(N) + 8 * 1024 <= device_info().smem_optin;
+}
+inline size_t eval8_smem_bytes(const pwl_table_s* t)
+{
+    return sizeof(float2) * (size_t)t->K + (forward_side_staged(t->N) ? forward_side_bytes(t->N) : 0);
+}
+// 16-byte index for the forward path: K_b cells and reserved chain records
+inline int64_t eval16_smem_records(const pwl_table_s* t)
 {
     const int64_t cap = (int64_t)(device_info().smem_optin / sizeof(float4));
-    return std::min<int64_t>(t->K + t->chain_reserve, cap);
+    return std::min<int64_t>(t->Kb + t->chain_reserve_b, cap);
 }
-inline size_t eval_smem_bytes(const pwl_table_s* t) { return sizeof(float4) * eval_smem_records(t); }
+inline size_t eval16_smem_bytes(const pwl_table_s* t) { return sizeof(float4) * (size_t)eval16_smem_records(t); }
 
-// Backward: records, N+2 reciprocal lengths and 2(N+2) FP32 accumulators.
+// cells of an 8-byte index that fit `budget` bytes next to the side records
+int64_t forward_cell_capacity(int64_t N, size_t budget);
+int64_t backward_cell_capacity(int64_t N);
+void choose_cells(pwl_table t, float hmin, int64_t requested);
+
+// Backward: K_b + reserved chain records, N+2 reciprocal lengths and
+// 2 (N+2) FP32 accumulators.  Chain records beyond the reserve are read from
+// global memory.
 inline size_t backward_fixed_smem(const pwl_table_s* t) { return 12 * (size_t)(t->N + 2); }
 inline int64_t backward_smem_records(const pwl_table_s* t)
 {
@@ -27,7 +43,7 @@ inline int64_t backward_smem_records(const pwl_table_s* t)
     const size_t fixed = backward_fixed_smem(t);
     if (fixed + 16 * 64 > optin) return -1;  // does not fit: unsupported
     const int64_t cap = (int64_t)((optin - fixed) / sizeof(float4));
-    return std::min<int64_t>(t->K + t->chain_reserve, cap);
+    return std::min<int64_t>(t->Kb + t->chain_reserve_b, cap);
 }
 inline size_t backward_smem_bytes(const pwl_table_s* t)
 {

@@ -130,12 +130,30 @@ def test_eval_small_case_both_forms(pwl, workloads):
 
 @pytest.mark.parametrize("k_cells", [1, 3, 17, 64, 1000, 9000])
 def test_eval_any_cell_count(pwl, workloads, k_cells):
-    # few cells force chains of many knots per cell; many cells none
+    # few cells force chains of many knots per cell; many cells none; both
+    # cell indexes (modes 2 and 3) are checked whichever pwl_eval picks
     f = workloads.LORENTZIAN
     t, xk, vk = _table_and_ref(pwl, f, 300, k_cells=k_cells)
     assert t.info["k_cells"] == k_cells
     x = workloads.uniform_queries(f, 100003, seed=7)
+    x[:xk.size] = torch.tensor(xk, dtype=torch.float32, device="cuda")
     _check_eval(t(x), xk, vk, x)
+    for mode in (2, 3):
+        y = t.variant(mode, x)
+        _check_eval(y, xk, vk, x)
+        # exact at the knots in either index
+        assert np.array_equal(y[:xk.size].cpu().numpy().astype(np.float64), vk)
+    t.close()
+
+
+@pytest.mark.parametrize("name", FUNCS)
+@pytest.mark.parametrize("N", [64, 1024, 4096])
+def test_eval_both_layouts_default_cells(pwl, workloads, name, N):
+    f = workloads.PAPER_FUNCTIONS[name]
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    x = workloads.normal_queries(f, (1 << 19) + 9, seed=4)
+    for mode in (2, 3):
+        _check_eval(t.variant(mode, x), xk, vk, x)
     t.close()
 
 
@@ -260,3 +278,64 @@ def test_invalid_arguments_are_rejected(pwl, workloads):
     v = torch.tensor([0.0, float("nan"), 2.0], dtype=torch.float64, device="cuda")
     with pytest.raises(PwlError):
         pwl.Table(k, v)
+
+
+def test_table_update_in_place(pwl, workloads):
+    # rebuild a table from new knots and values (same N): results follow the new function
+    f1, f2 = workloads.GAUSSIAN, dict(workloads.GAUSSIAN, p=[2.0, 0.5, 0.7])
+    N = 512
+    k1 = pwl.pwl_design(f1, N)
+    t = pwl.Table(k1, pwl.pwl_project(f1, k1, "project"))
+    k2 = pwl.pwl_design(f2, N)
+    v2 = pwl.pwl_project(f2, k2, "project")
+    t.update(k2, v2)
+    pwl.pwl_table_check(t.handle)
+    x = workloads.uniform_queries(f2, 300001, seed=9)
+    xk, vk = round_knots(k2.cpu().numpy()), round_values(v2.cpu().numpy(), "fp32")
+    _check_eval(t(x), xk, vk, x)
+    for mode in (2, 3):
+        _check_eval(t.variant(mode, x), xk, vk, x)
+    t.close()
+
+
+def test_design_projection_update_eval_in_a_cuda_graph(pwl, workloads):
+    # the asynchronous calls (design, projection, table update, evaluation)
+    # allocate nothing and never synchronize, so a stream capture replays them
+    f = workloads.BESSEL_J0
+    N = 1024
+    knots = pwl.pwl_design(f, N)
+    vals = pwl.pwl_project(f, knots, "project")
+    t = pwl.Table(knots, vals)
+    lib = __import__("paper_1510_02975_gb300._capi", fromlist=["load"]).load()
+    wsd = torch.empty(lib.pwl_design_workspace_size(N, 0), dtype=torch.uint8, device="cuda")
+    wsp = torch.empty(lib.pwl_project_workspace_size(N), dtype=torch.uint8, device="cuda")
+    x = workloads.uniform_queries(f, 1 << 20, seed=3)
+    y = torch.empty_like(x)
+
+    def body():
+        pwl.pwl_design(f, N, 0, "fp64", knots=knots, workspace=wsd)
+        pwl.pwl_project(f, knots, "project", values=vals, workspace=wsp)
+        t.update(knots, vals)
+        pwl.pwl_eval(t.handle, x, y)
+
+    body()
+    torch.cuda.synchronize()
+    y_eager = y.clone()
+    k_eager = knots.clone()
+    knots.zero_()
+    vals.zero_()
+    y.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            body()
+    torch.cuda.current_stream().wait_stream(s)
+    knots.zero_()
+    y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(knots, k_eager)
+    assert torch.equal(y, y_eager)
+    t.close()
