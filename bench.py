@@ -56,10 +56,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=21, help="oracle queries per (table, set)")
     ap.add_argument("--fwd-bwd-steps", type=int, default=3)
-    ap.add_argument("--report", default=None, choices=[None, "variants"],
+    ap.add_argument("--report", default=None, choices=[None, "variants", "channels"],
                     help="variants: per-table throughput of every evaluation path and the error of each "
                          "vertex-table precision (one JSON line)")
     ap.add_argument("--k-cells", type=int, default=0, help="cell count of the tables in --report variants")
+    ap.add_argument("--rows", type=int, default=65536, help="rows of x in --report channels")
     return ap.parse_args()
 
 
@@ -629,10 +630,58 @@ def run_variants(args):
                       "throughput": rows, "errors": errors}), flush=True)
 
 
+def run_channels(args):
+    """Channel-wise learnable map: x[65536, 4096] ~ N(0, 2^2) (FP32 and BF16),
+    4096 channels of 257 knots on [-8, 8] from the Gaussian design and P_T
+    values, perturbed per channel; forward, backward (x, values, knots) and
+    fwd+bwd throughput."""
+    import torch
+
+    import paper_1510_02975_gb300 as pwl
+    from paper_1510_02975_gb300 import _build
+    from paper_1510_02975_gb300 import workloads as W
+    _build.build()
+    R, C, N = args.rows, 4096, 256
+    f = {"kind": "gaussian", "a": -8.0, "b": 8.0, "p": [1.0, 0.0, 1.0]}
+    k64 = pwl.pwl_design(f, N)
+    v64 = pwl.pwl_project(f, k64, "project")
+    g = torch.Generator(device="cuda").manual_seed(4)
+    h = float(torch.diff(k64).min())
+    knots = k64.float().repeat(C, 1)
+    knots[:, 1:-1] += (torch.rand(C, N - 1, generator=g, device="cuda") - 0.5) * 0.4 * h
+    values = v64.float().repeat(C, 1) + torch.randn(C, N + 1, generator=g, device="cuda") * 1e-3
+    x = W.channel_inputs(R, C, seed=4)
+    gy = W.upstream_grad((R, C), seed=5)
+    y = torch.empty_like(x)
+    gx = torch.empty_like(x)
+    gv = torch.zeros_like(values)
+    gk = torch.zeros_like(knots)
+    xb = x.to(torch.bfloat16)
+    yb = torch.empty_like(xb)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    m = R * C
+    out = {}
+    for label, fn, nbytes in (
+            ("forward_fp32", lambda: pwl.pwl_channels_forward(knots, values, x, y, status=st), 8),
+            ("forward_bf16", lambda: pwl.pwl_channels_forward(knots, values, xb, yb, status=st), 4),
+            ("backward_fp32", lambda: pwl.pwl_channels_backward(knots, values, x, gy, gx, gv, gk, status=st), 12),
+            ("fwd_bwd_fp32", lambda: (pwl.pwl_channels_forward(knots, values, x, y, status=st),
+                                      pwl.pwl_channels_backward(knots, values, x, gy, gx, gv, gk, status=st)), 20)):
+        sec = time_launches(fn)
+        out[label] = {"G_evals_per_s": round(m / sec / 1e9, 2), "gbs": round(nbytes * m / sec / 1e9, 1),
+                      "ms": round(sec * 1e3, 4), "bytes_per_eval": nbytes}
+    peak, kind = measured_peaks()
+    print(json.dumps({"report": "channels", "shape": [R, C], "knots_per_channel": N + 1, "peak_gbs": peak,
+                      "peak_kind": kind, "status": int(st.item()), "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.report == "variants":
         run_variants(args)
+        return
+    if args.report == "channels":
+        run_channels(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -232,6 +232,35 @@ pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, f
                              float* d_g_values, float* d_g_knots, int64_t m, void* d_workspace,
                              size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Channel-wise maps: one CPWL function per channel (Algorithm 1 per element) */
+/* ------------------------------------------------------------------------ */
+
+/* y[r, c] = v_c(x[r, c]) for a row-major x[rows, n_channels], where channel
+ * c is the CPWL function with FP32 knots d_knots[c, 0..N] and values
+ * d_values[c, 0..N] (device arrays [n_channels, N+1], e.g. learnable
+ * parameters).  Each CTA builds the cell index of 16 channels in shared
+ * memory (k_cells cells per channel, 0 selects 4 (N+1); cells holding
+ * several knots are walked).  io_dtype PWL_FP32 or PWL_BF16 (x and y alike);
+ * the arithmetic is FP32; clamping and NaN as in pwl_eval.  Knots must be
+ * strictly increasing per channel: a violation sets bit 0 of the device
+ * word *d_status (the caller zeroes it; results are then unspecified).
+ * Errors: PWL_ENOTSUP if 16 channels' index does not fit a CTA
+ * (16 (8 (k_cells + 2 (N+1)) + 4 (N+1)) bytes).                          */
+pwl_status pwl_channels_forward(const float* d_knots, const float* d_values, int64_t n_channels,
+                                int64_t n_intervals, int64_t k_cells, const void* d_x, void* d_y,
+                                int64_t rows, int32_t io_dtype, int32_t* d_status, void* stream);
+
+/* Backward of pwl_channels_forward (FP32 only): gx[r, c] = gy[r, c] * s,
+ * and for every channel d_g_values[c, j] += sum over rows of gy dy/dv_j,
+ * d_g_knots[c, j] += sum of gy dy/dx_j (the formulas of pwl_eval_backward;
+ * either may be NULL; accumulated with FP32 atomics, order-dependent at FP32
+ * rounding).  k_cells: 0 selects 2 (N+1).                                  */
+pwl_status pwl_channels_backward(const float* d_knots, const float* d_values, int64_t n_channels,
+                                 int64_t n_intervals, int64_t k_cells, const float* d_x, const float* d_gy,
+                                 float* d_gx, float* d_g_values, float* d_g_knots, int64_t rows,
+                                 int32_t* d_status, void* stream);
+
 /* pwl_eval_backward for callers that cannot allocate device memory (the
  * paper has no counterpart; this is a library concern): real-time loops that
  * fix their memory at start-up, code called back from a host framework that

@@ -17,7 +17,8 @@ from ._capi import DTYPES, FORMS, KINDS, PRECISIONS, PwlError, PwlTableInfo, che
 
 __all__ = [
     "PwlError", "pwl_design", "pwl_project", "pwl_table_build", "pwl_table_update", "pwl_table_check", "pwl_table_destroy", "pwl_table_get_info",
-    "pwl_eval", "pwl_eval_variant", "pwl_eval_backward", "pwl_eval_backward_noalloc", "Table", "design", "project", "PWLFunction",
+    "pwl_eval", "pwl_eval_variant", "pwl_eval_backward", "pwl_eval_backward_noalloc",
+    "pwl_channels_forward", "pwl_channels_backward", "ChannelPWL", "Table", "design", "project", "PWLFunction",
     "KINDS", "FORMS", "DTYPES", "PRECISIONS",
 ]
 
@@ -195,6 +196,43 @@ def pwl_eval_backward_noalloc(handle, x, gy, gx=None, g_values=None, g_knots=Non
     return gx
 
 
+def pwl_channels_forward(knots, values, x, y=None, k_cells: int = 0, status=None, stream=None):
+    """y[r, c] = v_c(x[r, c]); knots, values float32 [C, N+1]; x [R, C] float32 or bfloat16."""
+    torch = _torch()
+    _require(knots, torch.float32, "knots")
+    _require(values, torch.float32, "values", knots.numel())
+    C, n1 = knots.shape
+    if x.dim() != 2 or x.shape[1] != C or not x.is_contiguous() or not x.is_cuda:
+        raise ValueError("x must be a contiguous CUDA tensor [rows, C]")
+    if y is None:
+        y = torch.empty_like(x)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    io = {torch.float32: 0, torch.bfloat16: 1}[x.dtype]
+    check(load().pwl_channels_forward(_ptr(knots), _ptr(values), C, n1 - 1, k_cells, _ptr(x), _ptr(y), x.shape[0],
+                                      io, _ptr(status), _stream(stream)), "pwl_channels_forward")
+    return y
+
+
+def pwl_channels_backward(knots, values, x, gy, gx=None, g_values=None, g_knots=None, k_cells: int = 0,
+                          status=None, stream=None):
+    """Backward of pwl_channels_forward (FP32): returns gx; accumulates g_values, g_knots [C, N+1]."""
+    torch = _torch()
+    _require(knots, torch.float32, "knots")
+    _require(values, torch.float32, "values", knots.numel())
+    C, n1 = knots.shape
+    _require(x, torch.float32, "x")
+    _require(gy, torch.float32, "gy", x.numel())
+    if gx is None:
+        gx = torch.empty_like(x)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    check(load().pwl_channels_backward(_ptr(knots), _ptr(values), C, n1 - 1, k_cells, _ptr(x), _ptr(gy), _ptr(gx),
+                                       _ptr(g_values), _ptr(g_knots), x.shape[0], _ptr(status), _stream(stream)),
+          "pwl_channels_backward")
+    return gx
+
+
 # ----------------------------------------------------------------------------
 # convenience layer
 # ----------------------------------------------------------------------------
@@ -241,27 +279,65 @@ class Table:
             pass
 
 
+_FUNCS = {}
+
+
+def _autograd_classes():
+    """torch.autograd.Function subclasses, defined on first use."""
+    if _FUNCS:
+        return _FUNCS
+    torch = _torch()
+
+    class _TableFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, handle, g_values, g_knots):
+            ctx.save_for_backward(x)
+            ctx.handle, ctx.gv, ctx.gk = handle, g_values, g_knots
+            return pwl_eval(handle, x.contiguous())
+
+        @staticmethod
+        def backward(ctx, gy):
+            (x,) = ctx.saved_tensors
+            gx = pwl_eval_backward(ctx.handle, x.contiguous(), gy.contiguous(), None, ctx.gv, ctx.gk)
+            return gx, None, None, None
+
+    class _ChannelFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, knots, values, k_cells, k_cells_bwd):
+            ctx.save_for_backward(x, knots, values)
+            ctx.k_cells_bwd = k_cells_bwd
+            return pwl_channels_forward(knots, values, x.contiguous(), k_cells=k_cells)
+
+        @staticmethod
+        def backward(ctx, gy):
+            x, knots, values = ctx.saved_tensors
+            gv = torch.zeros_like(values) if ctx.needs_input_grad[2] else None
+            gk = torch.zeros_like(knots) if ctx.needs_input_grad[1] else None
+            gx = pwl_channels_backward(knots, values, x.contiguous(), gy.contiguous().float(), None, gv, gk,
+                                       k_cells=ctx.k_cells_bwd)
+            return gx, gk, gv, None, None
+
+    _FUNCS["table"] = _TableFn
+    _FUNCS["channels"] = _ChannelFn
+    return _FUNCS
+
+
 class PWLFunction:
-    """torch.autograd.Function over a Table: y = v(x), with gradients w.r.t.
-    x (and the table's values / knots through table_grads)."""
+    """y = v(x) through a Table with autograd: gradients flow to x; if
+    table_grads = (g_values, g_knots) FP32 tensors of N+1 are given, the
+    backward accumulates the table gradients into them."""
 
     @staticmethod
     def apply(table: Table, x, table_grads=None):
-        torch = _torch()
+        gv, gk = table_grads if table_grads is not None else (None, None)
+        return _autograd_classes()["table"].apply(x, table.handle, gv, gk)
 
-        class _F(torch.autograd.Function):
-            @staticmethod
-            def forward(ctx, xx):
-                ctx.save_for_backward(xx)
-                return pwl_eval(table.handle, xx.contiguous())
 
-            @staticmethod
-            def backward(ctx, gy):
-                (xx,) = ctx.saved_tensors
-                gv = gk = None
-                if table_grads is not None:
-                    gv, gk = table_grads
-                gx = pwl_eval_backward(table.handle, xx.contiguous(), gy.contiguous(), None, gv, gk)
-                return gx
+class ChannelPWL:
+    """Channel-wise learnable CPWL map with autograd: y[r, c] = v_c(x[r, c])
+    for x [R, C] (float32), knots and values [C, N+1] (float32 leaf tensors).
+    The backward gives gradients w.r.t. x, the values and the knots."""
 
-        return _F.apply(x)
+    @staticmethod
+    def apply(x, knots, values, k_cells: int = 0, k_cells_backward: int = 0):
+        return _autograd_classes()["channels"].apply(x, knots, values, k_cells, k_cells_backward)

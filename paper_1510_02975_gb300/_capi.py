@@ -63,6 +63,8 @@ SIGNATURES = {
     "pwl_eval_backward_workspace_size": (_SZ, [_P]),
     "pwl_eval_backward": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P, _SZ, _P]),
     "pwl_eval_backward_noalloc": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P]),
+    "pwl_channels_forward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P, _P]),
+    "pwl_channels_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _I64, _P, _P]),
 }
 
 _lib = None

@@ -1,0 +1,593 @@
+// pwl_channels.cu -- channel-wise CPWL map: y[r, c] = v_c(x[r, c]) for a
+// row-major x[R, C] with one CPWL function per channel (Algorithm 1 per
+// element), and its backward (gradients w.r.t. x, the vertex values and the
+// knots of every channel).  The knots and values are plain FP32 device
+// arrays [C, N+1] (learnable parameters that change every step), so each CTA
+// builds the cell index of its channels in shared memory when it starts.
+//
+// Layout: a CTA owns a tile of 16 consecutive channels; a warp covers two
+// rows of the tile (lane = row_half * 16 + channel), so every global access
+// is a 64-byte row segment and the 16 lanes of a half-warp always address 16
+// different channels.  The per-channel indexes are stored channel-interleaved
+// (entry e of channel ch at [e * 16 + ch]), so a half-warp's shared-memory
+// accesses hit 16 different banks whatever cells or knots they look up.
+//
+// Forward index per channel: the 8-byte cell index of the single-table path
+// (cell records {y_c, s} or {knot tag, x_k}; side records {v_k, s_k},
+// {v_k, s_{k+1}}).  Backward index per channel: cell records {i, x_{i-1}}
+// for cells inside interval i or {knot tag, x_k}; interval records
+// {s_i, 1/h_i}.
+//
+// Work: the grid is made of 2-CTA clusters; a cluster takes a pair of
+// adjacent tiles (32 channels, 128-byte row segments) and its two CTAs walk
+// the same rows at the same time, one tile each, so that the two halves of
+// every 128-byte line of x are read while it is in L2 (one CTA alone would
+// leave the other half to a CTA that reads it much later, and the line would
+// be fetched twice).  Units = (tile pair, chunk of rows), pair-major; each
+// cluster takes a contiguous range of units and rebuilds its indexes only
+// when the pair changes.
+#include <math.h>
+
+#include <algorithm>
+
+#include "pwl_channels.cuh"
+
+namespace pwl {
+
+namespace {
+
+constexpr int kCh = 16;  // channels per tile
+constexpr int kChThreads = 1024;
+constexpr int kRowsPerPass = kChThreads / kCh;  // 64 rows per pass of the CTA
+constexpr int kChUnroll = 16;                    // passes in flight per thread (64 KB per SM)
+
+struct TileParams {
+    float a[kCh], b[kCh], inv_w[kCh], off[kCh], w[kCh];
+    int max_chain[kCh];
+    int any_chain;
+    int bad;
+};
+
+__device__ __forceinline__ int lower_bound_cells(const int* cj, int n, int v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (cj[mid * kCh] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Slopes are FP32 IEEE divisions of the FP32 differences: at most ~2 ulp
+// from the exact slope of the FP32 table, which moves a lerped value by
+// ~2^-23 |v_i - v_{i-1}| (FP64 would cost a slow FP64 division per record on
+// this GPU's few FP64 units).
+
+// Builds the index of channels [c0, c0 + 16) in shared memory.
+//   sP[cell * 16 + ch]      cell records
+//   sX[e * 16 + ch]         forward: side records e = 2k + side (2 (N+1));
+//                           backward: interval records e = i (N+2)
+//   xs[j * 16 + ch]         the tile's knots (staged first, coalesced)
+//   cj[j * 16 + ch]         scratch: first the tile's values, then the cell of knot j
+// Every global read is a coalesced pass over the tile's knots and values;
+// the rest works in shared memory.
+template <bool BWD>
+__device__ void build_tile(const ChanArgs& p, int64_t c0, float2* sP, float2* sX, float* xs, int* cj,
+                           TileParams* tp)
+{
+    const int N = p.N, K = p.K, n1 = N + 1;
+    const int nch = (int)min((int64_t)kCh, p.C - c0);
+    float* vs = reinterpret_cast<float*>(cj);
+    for (int e = threadIdx.x; e < kCh * n1; e += blockDim.x) {
+        const int ch = e / n1, j = e % n1;  // j fastest: consecutive threads read consecutive knots
+        float xv, vv;
+        if (ch < nch) {
+            xv = p.knots[(c0 + ch) * (int64_t)n1 + j];
+            vv = p.values[(c0 + ch) * (int64_t)n1 + j];
+        } else {  // padding channel of a partial tile: an unused identity on [0, 1]
+            xv = (float)j / (float)N;
+            vv = 0.0f;
+        }
+        xs[j * kCh + ch] = xv;
+        vs[j * kCh + ch] = vv;
+    }
+    if (threadIdx.x == 0) {
+        tp->any_chain = 0;
+        tp->bad = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < kCh) {
+        const int ch = threadIdx.x;
+        const float a = xs[ch], b = xs[N * kCh + ch];
+        tp->a[ch] = a;
+        tp->b[ch] = b;
+        tp->inv_w[ch] = (float)K / (b - a);
+        tp->off[ch] = -a * tp->inv_w[ch];
+        tp->w[ch] = (b - a) / (float)K;
+        tp->max_chain[ch] = 0;
+    }
+    // side (forward) or interval (backward) records, from the staged arrays
+    const int nx = BWD ? (N + 2) : 2 * n1;
+    for (int e = threadIdx.x; e < nx * kCh; e += blockDim.x) {
+        const int q = e / kCh, ch = e % kCh;
+        float2 rec;
+        if (BWD) {  // interval q (0 and N+1 copy 1 and N)
+            const int i = min(max(q, 1), N);
+            const float h = __fsub_rn(xs[i * kCh + ch], xs[(i - 1) * kCh + ch]);
+            rec = make_float2(__fdiv_rn(__fsub_rn(vs[i * kCh + ch], vs[(i - 1) * kCh + ch]), h), __frcp_rn(h));
+        } else {    // side record of knot k = q / 2
+            const int k = q >> 1;
+            const int i = (q & 1) ? min(k + 1, N) : max(k, 1);
+            const float h = __fsub_rn(xs[i * kCh + ch], xs[(i - 1) * kCh + ch]);
+            rec = make_float2(vs[k * kCh + ch], __fdiv_rn(__fsub_rn(vs[i * kCh + ch], vs[(i - 1) * kCh + ch]), h));
+        }
+        sX[e] = rec;
+    }
+    __syncthreads();
+    // cells of the knots (overwrites the staged values)
+    for (int e = threadIdx.x; e < n1 * kCh; e += blockDim.x) {
+        const int j = e / kCh, ch = e % kCh;
+        const float xj = xs[e];
+        if (j > 0 && !(xj > xs[e - kCh])) atomicOr(&tp->bad, 1);
+        cj[e] = cell_of(xj, tp->inv_w[ch], tp->off[ch], K);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n1 * kCh; e += blockDim.x) {
+        const int j = e / kCh, ch = e % kCh;
+        if (j > 0 && cj[e] == cj[e - kCh]) {
+            int first = j;
+            while (first > 0 && cj[(first - 1) * kCh + ch] == cj[e]) --first;
+            atomicMax(&tp->max_chain[ch], j - first);
+            atomicOr(&tp->any_chain, 1);
+        }
+    }
+    for (int e = threadIdx.x; e < K * kCh; e += blockDim.x) {
+        const int c = e / kCh, ch = e % kCh;
+        const int lb = lower_bound_cells(cj + ch, n1, c);
+        float2 rec;
+        if (lb <= N && cj[lb * kCh + ch] == c) {
+            const bool chain = (lb < N && cj[(lb + 1) * kCh + ch] == c);
+            rec = make_float2(make_knot_tag(lb, chain), xs[lb * kCh + ch]);
+        } else if (BWD) {
+            const int i = lb;  // the cell lies inside interval i = [x_{i-1}, x_i]
+            rec = make_float2(__int_as_float(i), xs[(i - 1) * kCh + ch]);
+        } else {
+            // the line of interval j+1 through (x_j, v_j): {v_j, s_{j+1}} is the
+            // right side record of knot j; valued at the anchor x_c
+            const int j = lb - 1;
+            const float2 sr = sX[(2 * j + 1) * kCh + ch];
+            const float xc = __fmaf_rn(__int2float_rn(c), tp->w[ch], tp->a[ch]);
+            rec = make_float2(__fmaf_rn(__fsub_rn(xc, xs[j * kCh + ch]), sr.y, sr.x), sr.y);
+        }
+        sP[e] = rec;
+    }
+    __syncthreads();
+}
+
+// A thread's channel is fixed for a tile: its constants live in registers.
+struct ChanConst {
+    float a, b, inv_w, off, w;
+    int max_chain;
+    __device__ __forceinline__ ChanConst(const TileParams& tp, int ch)
+        : a(tp.a[ch]), b(tp.b[ch]), inv_w(tp.inv_w[ch]), off(tp.off[ch]), w(tp.w[ch]), max_chain(tp.max_chain[ch])
+    {
+    }
+};
+
+template <bool CHAINS>
+__device__ __forceinline__ float chan_fwd_one(float x, int ch, const float* __restrict__ xs, const float2* sP,
+                                              const float2* sS, const ChanConst& cc, int N, int K)
+{
+    const float xc = clamp_nan(x, cc.a, cc.b);
+    const int c = cell_of(xc, cc.inv_w, cc.off, K);
+    const float2 r = sP[c * kCh + ch];
+    const uint32_t bits = __float_as_uint(r.x);
+    float anchor = __fmaf_rn(__int2float_rn(c), cc.w, cc.a);
+    float2 q = r;
+    if ((bits & 0xFFC00000u) == kLinkTag) {
+        int k = (int)(bits & kKnotTagMask);
+        float xk = r.y;
+        if (CHAINS && (bits & kKnotTagChain)) {
+            for (int g = 0; g < cc.max_chain && k < N; ++g) {
+                const float xn = xs[(k + 1) * kCh + ch];
+                if (!(xc >= xn)) break;
+                ++k;
+                xk = xn;
+            }
+        }
+        q = sS[(2 * k + (xc >= xk ? 1 : 0)) * kCh + ch];
+        anchor = xk;
+    }
+    return __fmaf_rn(xc - anchor, q.y, q.x);
+}
+
+template <typename IO>
+__device__ __forceinline__ float to_f32(IO v);
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename IO>
+__device__ __forceinline__ IO from_f32(float v);
+template <>
+__device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ void st_cs(float* p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st_cs(__nv_bfloat16* p, __nv_bfloat16 v) { *p = v; }
+
+template <typename IO, bool CHAINS>
+__device__ __forceinline__ void chan_fwd_rows(const ChanArgs& p, int64_t c0, int64_t r0, int64_t r1,
+                                              const float2* sP, const float2* sS, const float* xs,
+                                              const TileParams& tp, const IO* __restrict__ x, IO* __restrict__ y)
+{
+    const int ch = threadIdx.x % kCh;
+    const int64_t c = c0 + ch;
+    if (c >= p.C) return;
+    const ChanConst cc(tp, ch);
+    int64_t r = r0 + threadIdx.x / kCh;
+    const int64_t pass = (int64_t)kRowsPerPass * p.C;  // elements between a thread's consecutive rows
+    const IO* px = x + r * p.C + c;
+    IO* py = y + r * p.C + c;
+    for (; r + (int64_t)(kChUnroll - 1) * kRowsPerPass < r1; r += (int64_t)kChUnroll * kRowsPerPass) {
+        float v[kChUnroll];
+#pragma unroll
+        for (int u = 0; u < kChUnroll; ++u) v[u] = to_f32<IO>(px[u * pass]);
+#pragma unroll
+        for (int u = 0; u < kChUnroll; ++u) v[u] = chan_fwd_one<CHAINS>(v[u], ch, xs, sP, sS, cc, p.N, p.K);
+#pragma unroll
+        for (int u = 0; u < kChUnroll; ++u) st_cs(py + u * pass, from_f32<IO>(v[u]));
+        px += kChUnroll * pass;
+        py += kChUnroll * pass;
+    }
+    for (; r < r1; r += kRowsPerPass, px += pass, py += pass)
+        *py = from_f32<IO>(chan_fwd_one<CHAINS>(to_f32<IO>(*px), ch, xs, sP, sS, cc, p.N, p.K));
+}
+
+template <typename IO>
+__global__ void __launch_bounds__(kChThreads, 1) channels_forward_kernel(const ChanArgs p, const IO* x, IO* y)
+{
+    extern __shared__ float4 s_ch[];
+    float2* sP = reinterpret_cast<float2*>(s_ch);
+    float2* sS = sP + (size_t)p.K * kCh;
+    float* xs = reinterpret_cast<float*>(sS + (size_t)2 * (p.N + 1) * kCh);
+    int* cj = reinterpret_cast<int*>(xs + (size_t)(p.N + 1) * kCh);
+    __shared__ TileParams tp;
+    const int64_t cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
+    const int64_t u0 = p.units * cluster / nclusters, u1 = p.units * (cluster + 1) / nclusters;
+    int64_t built = -1;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int64_t tile = 2 * (u / p.per_pair) + (blockIdx.x & 1), chunk = u % p.per_pair;
+        if (tile >= p.tiles) break;  // the odd tile out of an odd tile count
+        if (tile != built) {
+            __syncthreads();
+            build_tile<false>(p, tile * kCh, sP, sS, xs, cj, &tp);
+            if (threadIdx.x == 0 && tp.bad) atomicOr(p.status, 1);
+            built = tile;
+        }
+        const int64_t r0 = chunk * p.rows_per_unit, r1 = min(p.R, r0 + p.rows_per_unit);
+        if (tp.any_chain)
+            chan_fwd_rows<IO, true>(p, tile * kCh, r0, r1, sP, sS, xs, tp, x, y);
+        else
+            chan_fwd_rows<IO, false>(p, tile * kCh, r0, r1, sP, sS, xs, tp, x, y);
+    }
+}
+
+// ---- backward ----------------------------------------------------------------
+// gx = gy * s_i; per (channel, interval) sums A_i = sum gy (1 - delta) and
+// B_i = sum gy delta accumulate in shared memory (FP32 atomics); at the end
+// of a tile's rows they become g_v[j] += A_{j+1} + B_j (+ clamped terms) and
+// g_x[j] += -s_{j+1} A_{j+1} - s_j B_j, added to the global gradients.
+struct EndSums {
+    float left, right;
+};
+
+template <bool CHAINS>
+__device__ __forceinline__ float chan_bwd_one(float x, float g, int ch, const float* __restrict__ xs,
+                                              const float2* sP, const float2* sI, const ChanConst& cc, int N,
+                                              int K, float* accA, float* accB, EndSums& e)
+{
+    if (x != x) return x;  // NaN: no table contribution
+    if (x < cc.a) {
+        e.left += g;
+        return 0.0f;
+    }
+    if (x > cc.b) {
+        e.right += g;
+        return 0.0f;
+    }
+    const int c = cell_of(x, cc.inv_w, cc.off, K);
+    const float2 r = sP[c * kCh + ch];
+    const uint32_t bits = __float_as_uint(r.x);
+    int i;
+    float delta, one_minus;
+    float2 q;
+    if ((bits & 0xFFC00000u) != kLinkTag) {  // inside interval i: {i, x_{i-1}}
+        i = __float_as_int(r.x);
+        q = sI[i * kCh + ch];
+        delta = (x - r.y) * q.y;
+        one_minus = 1.0f - delta;
+    } else {
+        int k = (int)(bits & kKnotTagMask);
+        float xk = r.y;
+        if (CHAINS && (bits & kKnotTagChain)) {
+            for (int gg = 0; gg < cc.max_chain && k < N; ++gg) {
+                const float xn = xs[(k + 1) * kCh + ch];
+                if (!(x >= xn)) break;
+                ++k;
+                xk = xn;
+            }
+        }
+        if (x < xk) {  // interval k, measured from its right end
+            i = k;
+            q = sI[i * kCh + ch];
+            one_minus = (xk - x) * q.y;
+            delta = 1.0f - one_minus;
+        } else if (k < N) {
+            i = k + 1;
+            q = sI[i * kCh + ch];
+            delta = (x - xk) * q.y;
+            one_minus = 1.0f - delta;
+        } else {  // x == x_N
+            i = N;
+            q = sI[i * kCh + ch];
+            delta = 1.0f;
+            one_minus = 0.0f;
+        }
+    }
+    atomicAdd(accA + i * kCh + ch, g * one_minus);
+    atomicAdd(accB + i * kCh + ch, g * delta);
+    return g * q.x;
+}
+
+template <bool CHAINS>
+__device__ __forceinline__ void chan_bwd_rows(const ChanArgs& p, int64_t c0, int64_t r0, int64_t r1,
+                                              const float2* sP, const float2* sI, const float* xs,
+                                              const TileParams& tp, float* accA, float* accB,
+                                              const float* __restrict__ x, const float* __restrict__ gy,
+                                              float* __restrict__ gx)
+{
+    const int ch = threadIdx.x % kCh;
+    const int64_t c = c0 + ch;
+    EndSums e{0.0f, 0.0f};
+    if (c < p.C) {
+        const ChanConst cc(tp, ch);
+        int64_t r = r0 + threadIdx.x / kCh;
+        const int64_t pass = (int64_t)kRowsPerPass * p.C;
+        const int64_t o = r * p.C + c;
+        const float* px = x + o;
+        const float* pg = gy + o;
+        float* po = gx + o;
+        constexpr int U = kChUnroll / 2;  // two loads per element
+        for (; r + (int64_t)(U - 1) * kRowsPerPass < r1; r += (int64_t)U * kRowsPerPass) {
+            float xv[U], gv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                xv[u] = px[u * pass];
+                gv[u] = pg[u * pass];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                po[u * pass] = chan_bwd_one<CHAINS>(xv[u], gv[u], ch, xs, sP, sI, cc, p.N, p.K, accA, accB, e);
+            px += U * pass;
+            pg += U * pass;
+            po += U * pass;
+        }
+        for (; r < r1; r += kRowsPerPass, px += pass, pg += pass, po += pass)
+            *po = chan_bwd_one<CHAINS>(*px, *pg, ch, xs, sP, sI, cc, p.N, p.K, accA, accB, e);
+    }
+    // lanes ch and ch + 16 share a channel: one add each
+    if (e.left != 0.0f) atomicAdd(accA + 0 * kCh + ch, e.left);
+    if (e.right != 0.0f) atomicAdd(accA + (p.N + 1) * kCh + ch, e.right);
+}
+
+// Adds a tile's shared sums to the global gradients and clears them.
+__device__ void flush_tile(const ChanArgs& p, int64_t c0, const float2* sI, float* accA, float* accB,
+                           float* g_values, float* g_knots)
+{
+    __syncthreads();
+    const int N = p.N;
+    for (int e = threadIdx.x; e < (N + 1) * kCh; e += blockDim.x) {
+        const int j = e / kCh, ch = e % kCh;
+        const int64_t c = c0 + ch;
+        if (c >= p.C) continue;
+        const float A1 = (j < N) ? accA[(j + 1) * kCh + ch] : 0.0f;
+        const float Bj = (j > 0) ? accB[j * kCh + ch] : 0.0f;
+        float gv = A1 + Bj;
+        if (j == 0) gv += accA[0 * kCh + ch];
+        if (j == N) gv += accA[(N + 1) * kCh + ch];
+        if (g_values && gv != 0.0f) atomicAdd(g_values + c * (int64_t)(N + 1) + j, gv);
+        if (g_knots) {
+            const float gk = -sI[(j + 1) * kCh + ch].x * A1 - sI[j * kCh + ch].x * Bj;
+            if (gk != 0.0f) atomicAdd(g_knots + c * (int64_t)(N + 1) + j, gk);
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (N + 2) * kCh; e += blockDim.x) {
+        accA[e] = 0.0f;
+        accB[e] = 0.0f;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kChThreads, 1) channels_backward_kernel(const ChanArgs p, const float* x,
+                                                                          const float* gy, float* gx,
+                                                                          float* g_values, float* g_knots)
+{
+    extern __shared__ float4 s_ch[];
+    float2* sP = reinterpret_cast<float2*>(s_ch);
+    float2* sI = sP + (size_t)p.K * kCh;
+    float* accA = reinterpret_cast<float*>(sI + (size_t)(p.N + 2) * kCh);
+    float* accB = accA + (size_t)(p.N + 2) * kCh;
+    float* xs = accB + (size_t)(p.N + 2) * kCh;
+    int* cj = reinterpret_cast<int*>(accA);  // build scratch aliases the accumulators
+    __shared__ TileParams tp;
+    const int64_t cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
+    const int64_t u0 = p.units * cluster / nclusters, u1 = p.units * (cluster + 1) / nclusters;
+    int64_t built = -1;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int64_t tile = 2 * (u / p.per_pair) + (blockIdx.x & 1), chunk = u % p.per_pair;
+        if (tile >= p.tiles) break;  // the odd tile out of an odd tile count
+        if (tile != built) {
+            if (built >= 0) flush_tile(p, built * kCh, sI, accA, accB, g_values, g_knots);
+            __syncthreads();
+            build_tile<true>(p, tile * kCh, sP, sI, xs, cj, &tp);
+            if (threadIdx.x == 0 && tp.bad) atomicOr(p.status, 1);
+            for (int e = threadIdx.x; e < (p.N + 2) * kCh; e += blockDim.x) {
+                accA[e] = 0.0f;
+                accB[e] = 0.0f;
+            }
+            __syncthreads();
+            built = tile;
+        }
+        const int64_t r0 = chunk * p.rows_per_unit, r1 = min(p.R, r0 + p.rows_per_unit);
+        if (tp.any_chain)
+            chan_bwd_rows<true>(p, tile * kCh, r0, r1, sP, sI, xs, tp, accA, accB, x, gy, gx);
+        else
+            chan_bwd_rows<false>(p, tile * kCh, r0, r1, sP, sI, xs, tp, accA, accB, x, gy, gx);
+    }
+    if (built >= 0) flush_tile(p, built * kCh, sI, accA, accB, g_values, g_knots);
+}
+
+}  // namespace
+
+size_t channels_smem_bytes(int64_t N, int64_t K, bool backward)
+{
+    const size_t n1 = (size_t)(N + 1), n2 = (size_t)(N + 2);
+    const size_t knots = sizeof(float) * kCh * n1;  // staged knots
+    if (!backward) return sizeof(float2) * kCh * ((size_t)K + 2 * n1) + 2 * knots;  // + values / cells
+    return sizeof(float2) * kCh * ((size_t)K + n2) + sizeof(float) * 2 * kCh * n2 + knots;
+}
+
+int64_t channels_default_cells(int64_t N, bool backward)
+{
+    // 4 (N+1) cells forward, 2 (N+1) backward, as far as one CTA's shared memory allows
+    const size_t budget = device_info().smem_optin - sizeof(float) * 256;  // static tile parameters
+    int64_t K = (backward ? 2 : 4) * (N + 1);
+    while (K > 16 && channels_smem_bytes(N, K, backward) > budget) K -= 16;
+    return K;
+}
+
+pwl_status channels_launch(const ChanArgs& base, bool backward, int io_dtype, const void* x, void* y,
+                           const float* gy, float* gx, float* g_values, float* g_knots, cudaStream_t s)
+{
+    ChanArgs p = base;
+    const size_t smem = channels_smem_bytes(p.N, p.K, backward);
+    const DeviceInfo& di = device_info();
+    if (smem > di.smem_optin)
+        return fail(PWL_ENOTSUP, "channel index of %zu bytes (16 channels x %d cells, N = %d) does not fit one CTA",
+                    smem, p.K, p.N);
+    p.tiles = (p.C + kCh - 1) / kCh;
+    const int64_t pairs = (p.tiles + 1) / 2;
+    const void* kfn;
+    if (backward)
+        kfn = (const void*)channels_backward_kernel;
+    else if (io_dtype == PWL_BF16)
+        kfn = (const void*)channels_forward_kernel<__nv_bfloat16>;
+    else
+        kfn = (const void*)channels_forward_kernel<float>;
+    PWL_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kChThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2);
+    int clusters = 0;
+    PWL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg));
+    clusters = std::max(clusters, 1);
+    // about 8 units per cluster: few index builds per CTA, and the last
+    // units balance the load
+    int64_t chunks = std::max<int64_t>(1, ((int64_t)clusters * 8 + pairs - 1) / pairs);
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, p.R / kRowsPerPass));
+    p.rows_per_unit = (p.R + chunks - 1) / chunks;
+    chunks = (p.R + p.rows_per_unit - 1) / p.rows_per_unit;
+    p.per_pair = chunks;
+    p.units = pairs * chunks;
+    clusters = (int)std::min<int64_t>(clusters, p.units);
+    cfg.gridDim = dim3(2 * clusters);
+    if (backward) {
+        PWL_CUDA_TRY(cudaLaunchKernelEx(&cfg, channels_backward_kernel, p, static_cast<const float*>(x), gy, gx,
+                                        g_values, g_knots));
+    } else if (io_dtype == PWL_BF16) {
+        PWL_CUDA_TRY(cudaLaunchKernelEx(&cfg, channels_forward_kernel<__nv_bfloat16>, p,
+                                        static_cast<const __nv_bfloat16*>(x), static_cast<__nv_bfloat16*>(y)));
+    } else {
+        PWL_CUDA_TRY(cudaLaunchKernelEx(&cfg, channels_forward_kernel<float>, p, static_cast<const float*>(x),
+                                        static_cast<float*>(y)));
+    }
+    PWL_CHECK_LAUNCH("channels kernel");
+    return PWL_OK;
+}
+
+}  // namespace pwl
+
+using namespace pwl;
+
+namespace {
+
+pwl_status check_channels(const float* knots, const float* values, int64_t C, int64_t N, int64_t R,
+                          int64_t k_cells, int32_t* d_status)
+{
+    if (!knots || !values) return fail(PWL_EINVAL, "knots / values is NULL");
+    if (C < 1 || N < 1 || N > 65535) return fail(PWL_EINVAL, "need C >= 1 channels and 1 <= N <= 65535 intervals");
+    if (R < 0) return fail(PWL_EINVAL, "rows must be >= 0");
+    if (k_cells < 0 || k_cells > (1 << 20)) return fail(PWL_EINVAL, "k_cells must be in [0, 2^20]");
+    if (!d_status) return fail(PWL_EINVAL, "status word is NULL");
+    return PWL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pwl_status pwl_channels_forward(const float* d_knots, const float* d_values, int64_t n_channels,
+                                int64_t n_intervals, int64_t k_cells, const void* d_x, void* d_y, int64_t rows,
+                                int32_t io_dtype, int32_t* d_status, void* stream)
+{
+    clear_error();
+    pwl_status st = check_channels(d_knots, d_values, n_channels, n_intervals, rows, k_cells, d_status);
+    if (st != PWL_OK) return st;
+    if (io_dtype != PWL_FP32 && io_dtype != PWL_BF16) return fail(PWL_EINVAL, "io dtype must be FP32 or BF16");
+    if (rows == 0) return PWL_OK;
+    if (!d_x || !d_y) return fail(PWL_EINVAL, "x / y is NULL");
+    ChanArgs p{};
+    p.knots = d_knots;
+    p.values = d_values;
+    p.C = n_channels;
+    p.R = rows;
+    p.N = (int)n_intervals;
+    p.K = (int)(k_cells > 0 ? k_cells : channels_default_cells(n_intervals, false));
+    p.status = d_status;
+    return channels_launch(p, false, io_dtype, d_x, d_y, nullptr, nullptr, nullptr, nullptr, as_stream(stream));
+}
+
+pwl_status pwl_channels_backward(const float* d_knots, const float* d_values, int64_t n_channels,
+                                 int64_t n_intervals, int64_t k_cells, const float* d_x, const float* d_gy,
+                                 float* d_gx, float* d_g_values, float* d_g_knots, int64_t rows, int32_t* d_status,
+                                 void* stream)
+{
+    clear_error();
+    pwl_status st = check_channels(d_knots, d_values, n_channels, n_intervals, rows, k_cells, d_status);
+    if (st != PWL_OK) return st;
+    if (rows == 0) return PWL_OK;
+    if (!d_x || !d_gy || !d_gx) return fail(PWL_EINVAL, "x / gy / gx is NULL");
+    ChanArgs p{};
+    p.knots = d_knots;
+    p.values = d_values;
+    p.C = n_channels;
+    p.R = rows;
+    p.N = (int)n_intervals;
+    p.K = (int)(k_cells > 0 ? k_cells : channels_default_cells(n_intervals, true));
+    p.status = d_status;
+    return channels_launch(p, true, PWL_FP32, d_x, nullptr, d_gy, d_gx, d_g_values, d_g_knots, as_stream(stream));
+}
+
+}  // extern "C"

@@ -212,12 +212,13 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_f_kernel(
             const bool chain = (lb < N && cj[lb + 1] == c);
             recP[c] = make_float2(make_knot_tag(lb, chain), xk[lb]);
         } else {
-            // the line of interval j+1 through (x_j, v_j), valued at the anchor x_c
+            // the line of interval j+1 through (x_j, v_j) with its FP32 slope,
+            // valued at the anchor x_c (FP32: one FP64 division per cell would
+            // dominate the build on this GPU's few FP64 units)
             const int j = lb - 1;
             const float xc = __fmaf_rn(__int2float_rn(c), w, a);
-            const double s = ((double)vk[j + 1] - (double)vk[j]) / ((double)xk[j + 1] - (double)xk[j]);
-            const double yc = (double)vk[j] + ((double)xc - (double)xk[j]) * s;
-            recP[c] = make_float2(__double2float_rn(yc), slope[j + 1]);
+            const float s = slope[j + 1];
+            recP[c] = make_float2(__fmaf_rn(__fsub_rn(xc, xk[j]), s, vk[j]), s);
         }
     }
     for (int k = threadIdx.x; k <= N; k += blockDim.x) {
