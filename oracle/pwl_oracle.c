@@ -255,7 +255,10 @@ void orc_gauss_legendre(int Q, double* nodes, double* weights)
 /* Load vector b_i = <f, phi_i> (Eq. 4 with the hat functions of Eq. 1), by
  * Q-point Gauss-Legendre quadrature on every interval I_j = [x_{j-1}, x_j]:
  * on I_j only phi_{j-1} = (x_j - t)/h_j and phi_j = (t - x_{j-1})/h_j are
- * non-zero.                                                                 */
+ * non-zero.  At the node t = mid + (h_j/2) xi_q these are exactly
+ * (1 - xi_q)/2 and (1 + xi_q)/2; the oracle uses those values, because
+ * forming x_j - t in floating point cancels (it loses about |x|/h_j ulps
+ * when the knots are far from 0 compared with h_j).                         */
 void orc_load_vector(const orc_func* F, const double* knots, int64_t N, int Q, double* bvec)
 {
     double xi[64], w[64];
@@ -268,8 +271,8 @@ void orc_load_vector(const orc_func* F, const double* knots, int64_t N, int Q, d
         for (int q = 0; q < Q; ++q) {
             double t = mid + half * xi[q];
             double fw = half * w[q] * orc_f(F, t);
-            bvec[j - 1] += fw * (xr - t) / h;
-            bvec[j] += fw * (t - xl) / h;
+            bvec[j - 1] += fw * ((1.0 - xi[q]) * 0.5);
+            bvec[j] += fw * ((1.0 + xi[q]) * 0.5);
         }
     }
 }
