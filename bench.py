@@ -56,11 +56,15 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=21, help="oracle queries per (table, set)")
     ap.add_argument("--fwd-bwd-steps", type=int, default=3)
-    ap.add_argument("--report", default=None, choices=[None, "variants", "channels"],
+    ap.add_argument("--report", default=None, choices=[None, "variants", "channels", "batched"],
                     help="variants: per-table throughput of every evaluation path and the error of each "
                          "vertex-table precision (one JSON line)")
     ap.add_argument("--k-cells", type=int, default=0, help="cell count of the tables in --report variants")
     ap.add_argument("--rows", type=int, default=65536, help="rows of x in --report channels")
+    ap.add_argument("--batch-funcs", type=int, default=4096, help="functions in --report batched")
+    ap.add_argument("--batch-m", type=int, default=16, help="density cells per interval in --report batched")
+    ap.add_argument("--no-per-function", action="store_true",
+                    help="--report batched: skip the one-table-per-function comparison")
     return ap.parse_args()
 
 
@@ -675,6 +679,130 @@ def run_channels(args):
                       "peak_kind": kind, "status": int(st.item()), "results": out}), flush=True)
 
 
+def f64_desc(desc, x):
+    """FP64 f for a function descriptor (numpy / scipy, not the oracle)."""
+    p = desc["p"]
+    if desc["kind"] == "gaussian":
+        u = (x - p[1]) / p[2]
+        return p[0] * np.exp(-0.5 * u * u)
+    if desc["kind"] == "lorentzian":
+        u = (x - p[1]) / p[2]
+        return p[0] / (1.0 + u * u)
+    from scipy.special import j0
+    return p[0] * j0(p[1] * x)
+
+
+def run_batched(args):
+    """Batches of independent functions: 4096 functions (Gaussians, sigma
+    log-uniform on [0.1, 10]; Lorentzians, gamma log-uniform on [0.1, 10];
+    J0(alpha x), alpha uniform on [0.5, 5]), N_f + 1 uniform on 16..4096
+    knots, log-uniform 10^3..10^6 FP32 queries per function uniform on its
+    domain.  A step is design (FP32 density, FP64 scan and inversion),
+    P_T values (FP32 integrand, FP64 sums and solve), index build and
+    evaluation of every query, captured in one CUDA graph."""
+    import torch
+
+    import paper_1510_02975_gb300 as pwl
+    from paper_1510_02975_gb300 import _build
+    from paper_1510_02975_gb300 import workloads as W
+    _build.build()
+    funcs, n_int, n_q = W.batch_functions(args.batch_funcs, seed=3)
+    x, qo = W.batch_queries(funcs, n_q, seed=6)
+    y = torch.empty_like(x)
+    nq = int(qo[-1])
+    b = pwl.Batch(funcs, n_int, m_per_interval=args.batch_m)
+    prec = "fp32"
+
+    def pipeline(stream=None):
+        b.design(prec, stream)
+        b.project("project", 8, prec, stream)
+        b.build(stream)
+
+    pipeline()
+    b.check()
+    b.plan(qo)
+    b.eval(x, y)
+    tune = b.autotune(x, y, reps=2)
+    info = b.info()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s, capture_error_mode="thread_local"):
+            pipeline(s)
+            b.eval(x, y, s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    phases = {
+        "design": time_launches(lambda: b.design(prec)),
+        "project": time_launches(lambda: b.project("project", 8, prec)),
+        "build": time_launches(lambda: b.build()),
+        "eval": time_launches(lambda: b.eval(x, y)),
+    }
+    step = time_launches(graph.replay, reps=max(args.steps, 3))
+    peak, kind = measured_peaks()
+    ev_gbs = BYTES_FWD * nq / phases["eval"] / 1e9
+    out = {
+        "report": "batched", "n_funcs": len(funcs), "total_knots": int(info["total_knots"]),
+        "total_queries": nq, "m_per_interval": args.batch_m,
+        "step_ms": round(step * 1e3, 4),
+        "step_G_evals_per_s": round(nq / step / 1e9, 2),
+        "phase_ms": {k: round(v * 1e3, 4) for k, v in phases.items()},
+        "eval": {"G_evals_per_s": round(nq / phases["eval"] / 1e9, 2), "gbs": round(ev_gbs, 1),
+                 "frac_of_peak": round(ev_gbs / peak, 4), "peak_gbs": peak, "peak_kind": kind,
+                 "grid": int(info["eval_grid"]), "threads": int(info["eval_threads"]),
+                 "shape": int(info["eval_shape"]), "stage_min": int(info["stage_min"]),
+                 "pieces": int(info["n_items"]), "staged_pieces": int(info["n_staged"]),
+                 "smem_bytes": int(info["smem_bytes"]), "index_bytes": int(info["index_bytes"]),
+                 "autotune_ms": {f"shape{k[0]}/stage{k[1]}": round(v, 4) for k, v in tune.items()}},
+    }
+    # error against FP64 f on the first 64 functions (4096 queries each)
+    yh_all = y[: min(nq, qo[64] if len(qo) > 64 else nq)].cpu().numpy().astype(np.float64)
+    xh_all = x[: yh_all.size].cpu().numpy().astype(np.float64)
+    err = {}
+    for fi in range(min(64, len(funcs))):
+        q0, q1 = qo[fi], min(qo[fi + 1], qo[fi] + 4096)
+        if q1 <= q0:
+            continue
+        e = float(np.abs(yh_all[q0:q1] - f64_desc(funcs[fi], xh_all[q0:q1])).max())
+        k = funcs[fi]["kind"]
+        err[k] = max(err.get(k, 0.0), e)
+    out["max_err_vs_f64_f_first64"] = err
+    if not args.no_per_function:
+        # the same evaluation as one pwl_eval launch per function (4096
+        # tables built from the batch's FP64 knots and values), the launches
+        # captured in one CUDA graph
+        kn = b.knots()
+        vv = b.values()
+        off = b.offsets()
+        tables = [pwl.Table(kn[off[f]:off[f + 1]], vv[off[f]:off[f + 1]]) for f in range(len(funcs))]
+        y2 = torch.empty_like(x)
+        g2 = torch.cuda.CUDAGraph()
+        s2 = torch.cuda.Stream()
+        for f, t in enumerate(tables):  # eager pass: kernel attributes set outside capture
+            if qo[f + 1] > qo[f]:
+                pwl.pwl_eval(t.handle, x[qo[f]:qo[f + 1]], y2[qo[f]:qo[f + 1]])
+        torch.cuda.synchronize()
+        s2.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s2):
+            with torch.cuda.graph(g2, stream=s2, capture_error_mode="thread_local"):
+                for f, t in enumerate(tables):
+                    if qo[f + 1] > qo[f]:
+                        pwl.pwl_eval(t.handle, x[qo[f]:qo[f + 1]], y2[qo[f]:qo[f + 1]], stream=s2)
+        torch.cuda.current_stream().wait_stream(s2)
+        sec = time_launches(g2.replay)
+        out["per_function_launches"] = {"G_evals_per_s": round(nq / sec / 1e9, 2),
+                                        "gbs": round(BYTES_FWD * nq / sec / 1e9, 1), "ms": round(sec * 1e3, 4),
+                                        "launches": sum(1 for f in range(len(funcs)) if qo[f + 1] > qo[f])}
+        # the two index different cell grids: equal up to FP32 rounding
+        out["per_function_launches"]["max_abs_diff_vs_batched"] = float((y - y2).abs().max())
+        for t in tables:
+            t.close()
+    b.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.report == "variants":
@@ -682,6 +810,9 @@ def main():
         return
     if args.report == "channels":
         run_channels(args)
+        return
+    if args.report == "batched":
+        run_batched(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -233,6 +233,114 @@ pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, f
                              size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batches: many independent functions, each with its own partition          */
+/* ------------------------------------------------------------------------ */
+
+/* A batch holds F functions f_0..f_{F-1}, function f with its own interval
+ * I_f and N_f intervals (Section II-B for each).  Its device arrays are
+ * concatenated in function order: knots and values of function f occupy
+ * entries koff[f] .. koff[f] + N_f, koff[f] = sum_{g<f} (N_g + 1).  Each
+ * phase is one fixed sequence of launches over all functions, enqueued
+ * without host synchronisation, so that design, projection, index build and
+ * evaluation can be captured in one CUDA graph and replayed.
+ *   funcs          host, F descriptors (validated as for pwl_design)
+ *   n_intervals    host, F values N_f in [1, 65535]
+ *   m_per_interval density cells per interval of the design step
+ *                  (M_f = m_per_interval N_f); 0 selects 64
+ *   cells_per_knot cells of each function's evaluation index per knot
+ *                  (0 selects 4), reduced where the index would not leave
+ *                  room for two CTAs per SM
+ * Allocates all device memory of the batch (synchronously); the batch owns
+ * it until pwl_batch_destroy.  Errors: PWL_EINVAL (sizes, a descriptor),
+ * PWL_ENOMEM / PWL_ECUDA (allocation).                                      */
+pwl_status pwl_batch_create(const pwl_func* funcs, const int64_t* n_intervals, int64_t n_funcs,
+                            int64_t m_per_interval, int64_t cells_per_knot, pwl_batch* out);
+pwl_status pwl_batch_destroy(pwl_batch b);
+
+/* Knots of T* for every function (pwl_design per function, Eqs. 16-18, with
+ * M_f cells): the knots land in the batch's FP64 knot array.               */
+pwl_status pwl_batch_design(pwl_batch b, int32_t precision, void* stream);
+
+/* Vertex values of every function (pwl_project per function, Eqs. 3-6) from
+ * the batch's knots into its FP64 value array.                             */
+pwl_status pwl_batch_project(pwl_batch b, int32_t form, int32_t quad_points, int32_t precision,
+                             void* stream);
+
+/* Evaluation index of every function from the batch's FP64 knots and values
+ * (rounded to FP32; the CPWL function evaluated is exactly that rounded
+ * one).  Call after pwl_batch_design / pwl_batch_project, or after writing
+ * the FP64 arrays through pwl_batch_get_info.  Does not check the rounded
+ * knots (pwl_batch_check does).                                            */
+pwl_status pwl_batch_build(pwl_batch b, void* stream);
+
+/* PWL_EINVAL if the last build found a function whose rounded knots are not
+ * strictly increasing or a knot or value not finite (message names the
+ * first one); evaluation of such a function is unspecified.  PWL_ETIMEOUT
+ * if an evaluation since the last check gave up waiting for a staging copy
+ * (its results are then incomplete); the check clears that flag.
+ * Synchronizes `stream`.                                                    */
+pwl_status pwl_batch_check(pwl_batch b, void* stream);
+
+/* Plans evaluation for a query layout: function f's queries are
+ * x[query_offsets[f]] .. x[query_offsets[f+1] - 1] (host array of F+1
+ * non-decreasing offsets, query_offsets[0] = 0).  The concatenated stream
+ * is cut into one contiguous range per CTA of a persistent grid, of about
+ * equal cost; a CTA stages a function's index in shared memory when its
+ * share of the function's queries times stage_min is at least the index
+ * bytes (stage_min 0: never stage; -1: keep the current value, initially
+ * 16).  shape (-1 keeps the current one, initially 0):
+ *   0  one 1024-thread CTA per SM with two record buffers: a bulk copy
+ *      (cp.async.bulk) brings the next piece's records while the CTA
+ *      streams the current piece;
+ *   1  one 1024-thread CTA per SM, staging by the CTA's threads;
+ *   2  two 512-thread CTAs per SM, staging by the CTA's threads;
+ *   3  no staging: every piece reads its records through L1 (stage_min is
+ *      ignored).
+ * Allocates the plan (synchronously; the previous plan is freed).  A wait
+ * for a bulk copy gives up after 1 s; pwl_batch_check then reports
+ * PWL_ETIMEOUT.                                                             */
+pwl_status pwl_batch_plan(pwl_batch b, const int64_t* query_offsets, int32_t shape, int64_t stage_min);
+
+/* y[q] = v_f(x[q]) for every planned query (Algorithm 1 per function, the
+ * same arithmetic, clamping and NaN rule as pwl_eval): one persistent
+ * launch.  x, y: device FP32 arrays of query_offsets[F] elements, 16-byte
+ * aligned; y may be x.                                                      */
+pwl_status pwl_batch_eval(pwl_batch b, const float* d_x, float* d_y, void* stream);
+
+/* Autotuner: times pwl_batch_eval on the caller's x and y (reps timed
+ * launches per candidate after one warm-up) for every CTA shape (0..3) and
+ * staging threshold stage_min in {0, 4, 16, 64}, and keeps the fastest plan.
+ * timings_ms: host array of 16 floats receiving the mean launch time of
+ * candidate (shape, threshold) at index 4 shape + threshold position, or
+ * NULL.  Writes y; synchronizes `stream`; must not run during stream
+ * capture.                                                                  */
+pwl_status pwl_batch_autotune(pwl_batch b, const float* d_x, float* d_y, int32_t reps, float* timings_ms,
+                              void* stream);
+
+typedef struct {
+    int64_t n_funcs;
+    int64_t total_knots;     /* sum of N_f + 1 */
+    int64_t total_cells;     /* cells of all evaluation indexes */
+    int64_t index_bytes;     /* bytes of all evaluation indexes */
+    int64_t total_queries;   /* of the current plan (0 before pwl_batch_plan) */
+    int32_t eval_grid;       /* CTAs of the evaluation launch */
+    int32_t eval_threads;    /* threads per CTA */
+    int32_t eval_shape;
+    int32_t reserved;
+    int64_t n_items;         /* (function, query range) pieces of the plan */
+    int64_t n_staged;        /* pieces that stage their function's index */
+    int64_t stage_min;
+    int64_t smem_bytes;      /* dynamic shared memory of the evaluation launch */
+    const int64_t* d_knot_offsets; /* device, F+1 offsets koff */
+    double* d_knots;         /* device, FP64 knots (written by pwl_batch_design) */
+    double* d_values;        /* device, FP64 values (written by pwl_batch_project) */
+    const float* d_knots_fp32;  /* device, FP32 knots of the last build */
+    const float* d_values_fp32; /* device, FP32 values of the last build */
+} pwl_batch_info;
+
+pwl_status pwl_batch_get_info(pwl_batch b, pwl_batch_info* info);
+
+/* ------------------------------------------------------------------------ */
 /* Channel-wise maps: one CPWL function per channel (Algorithm 1 per element) */
 /* ------------------------------------------------------------------------ */
 

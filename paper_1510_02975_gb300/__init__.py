@@ -13,11 +13,14 @@ from __future__ import annotations
 
 import ctypes
 
-from ._capi import DTYPES, FORMS, KINDS, PRECISIONS, PwlError, PwlTableInfo, check, load, make_func
+from ._capi import (DTYPES, FORMS, KINDS, PRECISIONS, PwlBatchInfo, PwlError, PwlFunc, PwlTableInfo, check, load,
+                    make_func)
 
 __all__ = [
     "PwlError", "pwl_design", "pwl_project", "pwl_table_build", "pwl_table_update", "pwl_table_check", "pwl_table_destroy", "pwl_table_get_info",
     "pwl_eval", "pwl_eval_variant", "pwl_eval_backward", "pwl_eval_backward_noalloc",
+    "pwl_batch_create", "pwl_batch_destroy", "pwl_batch_design", "pwl_batch_project", "pwl_batch_build",
+    "pwl_batch_check", "pwl_batch_plan", "pwl_batch_eval", "pwl_batch_autotune", "pwl_batch_get_info", "Batch",
     "pwl_channels_forward", "pwl_channels_backward", "ChannelPWL", "Table", "design", "project", "PWLFunction",
     "KINDS", "FORMS", "DTYPES", "PRECISIONS",
 ]
@@ -196,6 +199,86 @@ def pwl_eval_backward_noalloc(handle, x, gy, gx=None, g_values=None, g_knots=Non
     return gx
 
 
+def pwl_batch_create(funcs, n_intervals, m_per_interval: int = 0, cells_per_knot: int = 0):
+    """Opaque batch handle (int) for F function descriptors and their N_f."""
+    lib = load()
+    F = len(funcs)
+    if len(n_intervals) != F:
+        raise ValueError("one n_intervals entry per function")
+    arr = (PwlFunc * max(F, 1))()
+    for i, f in enumerate(funcs):
+        arr[i] = make_func(f)
+    ns = (ctypes.c_int64 * max(F, 1))(*[int(n) for n in n_intervals])
+    out = ctypes.c_void_p()
+    check(lib.pwl_batch_create(arr, ns, F, m_per_interval, cells_per_knot, ctypes.byref(out)), "pwl_batch_create")
+    return out.value
+
+
+def pwl_batch_destroy(handle) -> None:
+    if handle:
+        check(load().pwl_batch_destroy(ctypes.c_void_p(handle)), "pwl_batch_destroy")
+
+
+def pwl_batch_design(handle, precision: str = "fp64", stream=None) -> None:
+    check(load().pwl_batch_design(ctypes.c_void_p(handle), PRECISIONS[precision], _stream(stream)),
+          "pwl_batch_design")
+
+
+def pwl_batch_project(handle, form: str = "project", quad_points: int = 8, precision: str = "fp64",
+                      stream=None) -> None:
+    check(load().pwl_batch_project(ctypes.c_void_p(handle), FORMS[form], quad_points, PRECISIONS[precision],
+                                   _stream(stream)), "pwl_batch_project")
+
+
+def pwl_batch_build(handle, stream=None) -> None:
+    check(load().pwl_batch_build(ctypes.c_void_p(handle), _stream(stream)), "pwl_batch_build")
+
+
+def pwl_batch_check(handle, stream=None) -> None:
+    check(load().pwl_batch_check(ctypes.c_void_p(handle), _stream(stream)), "pwl_batch_check")
+
+
+def pwl_batch_plan(handle, query_offsets, shape: int = -1, stage_min: int = -1) -> None:
+    """query_offsets: F+1 non-decreasing ints (host sequence), first 0."""
+    qo = (ctypes.c_int64 * len(query_offsets))(*[int(q) for q in query_offsets])
+    check(load().pwl_batch_plan(ctypes.c_void_p(handle), qo, shape, stage_min), "pwl_batch_plan")
+
+
+def pwl_batch_eval(handle, x, y=None, stream=None):
+    torch = _torch()
+    _require(x, torch.float32, "x")
+    planned = pwl_batch_get_info(handle)["total_queries"]
+    if x.numel() < planned:
+        raise ValueError(f"x has {x.numel()} elements; the plan has {planned} queries")
+    if y is None:
+        y = torch.empty_like(x)
+    _require(y, torch.float32, "y", x.numel())
+    check(load().pwl_batch_eval(ctypes.c_void_p(handle), _ptr(x), _ptr(y), _stream(stream)), "pwl_batch_eval")
+    return y
+
+
+def pwl_batch_autotune(handle, x, y, reps: int = 3, stream=None) -> dict:
+    """Times every (shape, stage_min) candidate, keeps the fastest plan and
+    returns {(shape, stage_min): mean ms per launch}."""
+    torch = _torch()
+    _require(x, torch.float32, "x")
+    planned = pwl_batch_get_info(handle)["total_queries"]
+    if x.numel() < planned:
+        raise ValueError(f"x has {x.numel()} elements; the plan has {planned} queries")
+    _require(y, torch.float32, "y", x.numel())
+    t = (ctypes.c_float * 16)()
+    check(load().pwl_batch_autotune(ctypes.c_void_p(handle), _ptr(x), _ptr(y), reps, t, _stream(stream)),
+          "pwl_batch_autotune")
+    return {(shape, stage_min): float(t[4 * shape + j])
+            for shape in range(4) for j, stage_min in enumerate((0, 4, 16, 64))}
+
+
+def pwl_batch_get_info(handle) -> dict:
+    info = PwlBatchInfo()
+    check(load().pwl_batch_get_info(ctypes.c_void_p(handle), ctypes.byref(info)), "pwl_batch_get_info")
+    return {k: getattr(info, k) for k, _ in PwlBatchInfo._fields_}
+
+
 def pwl_channels_forward(knots, values, x, y=None, k_cells: int = 0, status=None, stream=None):
     """y[r, c] = v_c(x[r, c]); knots, values float32 [C, N+1]; x [R, C] float32 or bfloat16."""
     torch = _torch()
@@ -270,6 +353,83 @@ class Table:
     def close(self):
         if getattr(self, "handle", None):
             pwl_table_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent CPWL functions on the GPU (owns a pwl_batch)."""
+
+    def __init__(self, funcs, n_intervals, m_per_interval: int = 0, cells_per_knot: int = 0):
+        self.handle = pwl_batch_create(funcs, n_intervals, m_per_interval, cells_per_knot)
+        self.n_funcs = len(funcs)
+        self.n_intervals = [int(n) for n in n_intervals]
+
+    def design(self, precision: str = "fp64", stream=None):
+        pwl_batch_design(self.handle, precision, stream)
+
+    def project(self, form: str = "project", quad_points: int = 8, precision: str = "fp64", stream=None):
+        pwl_batch_project(self.handle, form, quad_points, precision, stream)
+
+    def build(self, stream=None):
+        pwl_batch_build(self.handle, stream)
+
+    def check(self, stream=None):
+        pwl_batch_check(self.handle, stream)
+
+    def plan(self, query_offsets, shape: int = -1, stage_min: int = -1):
+        pwl_batch_plan(self.handle, query_offsets, shape, stage_min)
+
+    def eval(self, x, out=None, stream=None):
+        return pwl_batch_eval(self.handle, x, out, stream)
+
+    def autotune(self, x, y, reps: int = 3):
+        return pwl_batch_autotune(self.handle, x, y, reps)
+
+    def info(self) -> dict:
+        return pwl_batch_get_info(self.handle)
+
+    def _device_array(self, key, typestr, copy):
+        """The batch's concatenated device array `key` as a torch tensor:
+        a copy, or (copy=False) a view that the next design / projection /
+        build overwrites and that pwl_batch_destroy frees."""
+        torch = _torch()
+        info = self.info()
+
+        class _Cai:
+            __cuda_array_interface__ = {"shape": (int(info["total_knots"]),), "typestr": typestr,
+                                        "data": (int(info[key]), False), "version": 3}
+
+        t = torch.as_tensor(_Cai(), device="cuda")
+        return t.clone() if copy else t
+
+    def knots(self, copy: bool = True):
+        """float64 knots of all functions; function f's at offsets()[f]."""
+        return self._device_array("d_knots", "<f8", copy)
+
+    def values(self, copy: bool = True):
+        return self._device_array("d_values", "<f8", copy)
+
+    def knots_fp32(self, copy: bool = True):
+        return self._device_array("d_knots_fp32", "<f4", copy)
+
+    def values_fp32(self, copy: bool = True):
+        return self._device_array("d_values_fp32", "<f4", copy)
+
+    def offsets(self):
+        out = [0]
+        for n in self.n_intervals:
+            out.append(out[-1] + n + 1)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pwl_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

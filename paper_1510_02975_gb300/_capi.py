@@ -39,6 +39,16 @@ class PwlTableInfo(ctypes.Structure):
                 ("layout", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
+class PwlBatchInfo(ctypes.Structure):
+    _fields_ = [("n_funcs", ctypes.c_int64), ("total_knots", ctypes.c_int64), ("total_cells", ctypes.c_int64),
+                ("index_bytes", ctypes.c_int64), ("total_queries", ctypes.c_int64), ("eval_grid", ctypes.c_int32),
+                ("eval_threads", ctypes.c_int32), ("eval_shape", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_items", ctypes.c_int64), ("n_staged", ctypes.c_int64), ("stage_min", ctypes.c_int64),
+                ("smem_bytes", ctypes.c_int64), ("d_knot_offsets", ctypes.c_void_p), ("d_knots", ctypes.c_void_p),
+                ("d_values", ctypes.c_void_p), ("d_knots_fp32", ctypes.c_void_p),
+                ("d_values_fp32", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -63,6 +73,17 @@ SIGNATURES = {
     "pwl_eval_backward_workspace_size": (_SZ, [_P]),
     "pwl_eval_backward": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P, _SZ, _P]),
     "pwl_eval_backward_noalloc": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P]),
+    "pwl_batch_create": (_ST, [ctypes.POINTER(PwlFunc), ctypes.POINTER(_I64), _I64, _I64, _I64,
+                               ctypes.POINTER(_P)]),
+    "pwl_batch_destroy": (_ST, [_P]),
+    "pwl_batch_design": (_ST, [_P, _I32, _P]),
+    "pwl_batch_project": (_ST, [_P, _I32, _I32, _I32, _P]),
+    "pwl_batch_build": (_ST, [_P, _P]),
+    "pwl_batch_check": (_ST, [_P, _P]),
+    "pwl_batch_plan": (_ST, [_P, ctypes.POINTER(_I64), _I32, _I64]),
+    "pwl_batch_eval": (_ST, [_P, _P, _P, _P]),
+    "pwl_batch_autotune": (_ST, [_P, _P, _P, _I32, ctypes.POINTER(ctypes.c_float), _P]),
+    "pwl_batch_get_info": (_ST, [_P, ctypes.POINTER(PwlBatchInfo)]),
     "pwl_channels_forward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P, _P]),
     "pwl_channels_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _I64, _P, _P]),
 }

@@ -203,6 +203,466 @@ __global__ void invert_kernel(DesignPlan p)
     }
 }
 
+// ---- fused design of whole functions (batches) ----------------------------
+// One CTA designs one function at a time, in one launch for the batch:
+//   pass A  for every 2048-cell chunk: the densities (8 contiguous cells per
+//           thread), the chunk total (block scan in FP64) and the chunk's
+//           last cell of positive density;
+//   scan    exclusive FP64 scan of the chunk totals: chunk bases, G_M;
+//   pass B  for every chunk holding targets tau_i (G at the chunk start <=
+//           tau_i < G at the next chunk's start): the densities again, the
+//           FP64 prefix of the thread partials, and for each such knot the
+//           largest cell k with G_k <= tau_i (binary search over the thread
+//           prefixes, then the thread's cells), the walk back to a cell of
+//           positive density, and x_i = a + k delta + (tau_i - G_k) / d_k.
+// Nothing per cell goes to memory.  Thread partials of 8 densities are a
+// plain FP64 sum (FP64 mode) or a compensated FP32 sum (FP32 mode: two-sum,
+// every rounding error carried, about 2^-48 relative); all sums above them
+// are FP64.  In FP32 mode the cell midpoints are formed in FP32 from the
+// chunk start (the FP32 f'' rounds its argument to FP32 anyway).
+template <typename T>
+struct Partial;
+template <>
+struct Partial<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s = __dadd_rn(s, v); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Partial<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float t = __fadd_rn(s, v);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// The uncompensated running sum of a partial, in the density's type: the
+// cheap candidate of the in-thread cell search (checked in FP64 after).
+__device__ __forceinline__ double approx(const Partial<double>& p) { return p.s; }
+__device__ __forceinline__ float approx(const Partial<float>& p) { return p.s; }
+
+template <typename T>
+__device__ __forceinline__ T fused_density(const pwl_func& F, double a, double delta, int64_t k, float t0f,
+                                           float deltaf, int local);
+template <>
+__device__ __forceinline__ double fused_density<double>(const pwl_func& F, double a, double delta, int64_t k,
+                                                        float, float, int)
+{
+    const double t = __dadd_rn(a, __dmul_rn((double)k + 0.5, delta));
+    return pow(fabs(func_second_derivative<double>(F, t)), 0.4);
+}
+template <>
+__device__ __forceinline__ float fused_density<float>(const pwl_func& F, double, double, int64_t, float t0f,
+                                                      float deltaf, int local)
+{
+    const float t = __fmaf_rn((float)local + 0.5f, deltaf, t0f);
+    return powf(fabsf(func_second_derivative<float>(F, t)), 0.4f);
+}
+
+// smallest i in [1, N] with tau_i = i G_M / N >= G (N if none below N)
+__device__ __forceinline__ int64_t first_target_at_or_above(double G, double GM, int64_t N)
+{
+    auto tau = [&](int64_t i) { return (double)i * GM / (double)N; };
+    const double e = floor(G / GM * (double)N);
+    int64_t i = (int64_t)fmin(fmax(e, 1.0), (double)N);
+    while (i > 1 && tau(i - 1) >= G) --i;
+    while (i < N && tau(i) < G) ++i;
+    return i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan p)
+{
+    __shared__ T s_d[kChunk];
+    __shared__ double s_S[kDesignThreads];  // chunk base + exclusive prefix of the thread partials
+    __shared__ double s_G[kDesignThreads];  // delta * s_S: G at each thread's first cell
+    __shared__ double s_warp[kDesignThreads / 32 + 1];
+    __shared__ int s_last;
+    __shared__ int64_t s_range[2];
+    const int t = threadIdx.x;
+    for (int o = blockIdx.x; o < p.F; o += gridDim.x) {
+        const int f = p.order[o];
+        const pwl_func F = p.funcs[f];
+        const int64_t M = p.moff[f + 1] - p.moff[f];
+        const int64_t N = p.koff[f + 1] - p.koff[f] - 1;
+        const int64_t nch = p.choff[f + 1] - p.choff[f];
+        const double a = F.a, b = F.b;
+        const double delta = (b - a) / (double)M;
+        const float deltaf = (float)delta;
+        double* __restrict__ knots = p.knots + p.koff[f];
+        double* __restrict__ csum = p.csum + p.choff[f];
+        double* __restrict__ cbase = p.cbase + p.choff[f];
+        int* __restrict__ clast = p.clast + p.choff[f];
+
+        // pass A
+        for (int64_t ch = 0; ch < nch; ++ch) {
+            const int64_t c0 = ch * kChunk;
+            const int cnt = (int)min((int64_t)kChunk, M - c0);
+            const float t0f = (float)(a + (double)c0 * delta);
+            Partial<T> part;
+            int last = -1;
+            for (int r = 0; r < kPerThread; ++r) {
+                const int l = t * kPerThread + r;
+                if (l < cnt) {
+                    const T dk = fused_density<T>(F, a, delta, c0 + l, t0f, deltaf, l);
+                    part.add(dk);
+                    if (dk > T(0)) last = l;
+                }
+            }
+            if (t == 0) s_last = -1;
+            __syncthreads();
+            if (last >= 0) atomicMax(&s_last, last);
+            double tot;
+            block_exclusive_scan(part.value(), s_warp, &tot);
+            if (t == 0) {
+                csum[ch] = tot;
+                clast[ch] = s_last;
+            }
+        }
+        __syncthreads();
+        // exclusive scan of the chunk totals
+        double carry = 0.0;
+        for (int64_t base = 0; base < nch; base += kDesignThreads) {
+            const int64_t c = base + t;
+            const double v = c < nch ? csum[c] : 0.0;
+            double tot;
+            const double ex = block_exclusive_scan(v, s_warp, &tot);
+            if (c < nch) cbase[c] = carry + ex;
+            carry += tot;
+        }
+        __syncthreads();
+        const double GM = delta * carry;
+        if (t == 0) {
+            knots[0] = a;
+            knots[N] = b;
+        }
+        if (!(GM > 0.0)) {  // f linear on I (or no finite density): the uniform partition
+            for (int64_t i = 1 + t; i < N; i += kDesignThreads) knots[i] = a + (double)i * (b - a) / (double)N;
+            __syncthreads();
+            continue;
+        }
+
+        // pass B
+        int64_t lastpos = -1;  // last cell of positive density before the current chunk
+        for (int64_t ch = 0; ch < nch; ++ch) {
+            const int64_t c0 = ch * kChunk;
+            if (t == 0) {
+                s_range[0] = first_target_at_or_above(delta * cbase[ch], GM, N);
+                s_range[1] = ch + 1 < nch ? first_target_at_or_above(delta * cbase[ch + 1], GM, N) : N;
+            }
+            __syncthreads();
+            const int64_t i0 = s_range[0], i1 = s_range[1];
+            if (i0 < i1) {
+                const int cnt = (int)min((int64_t)kChunk, M - c0);
+                const float t0f = (float)(a + (double)c0 * delta);
+                Partial<T> part;
+                for (int r = 0; r < kPerThread; ++r) {
+                    const int l = t * kPerThread + r;
+                    if (l < cnt) {
+                        const T dk = fused_density<T>(F, a, delta, c0 + l, t0f, deltaf, l);
+                        s_d[l] = dk;
+                        part.add(dk);
+                    }
+                }
+                double tot;
+                const double ex = block_exclusive_scan(part.value(), s_warp, &tot);
+                s_S[t] = cbase[ch] + ex;
+                s_G[t] = delta * (cbase[ch] + ex);
+                __syncthreads();
+                const int U = (cnt + kPerThread - 1) / kPerThread;  // threads holding cells
+                // G at local cell l: delta * (S_u + partial of the thread's cells before l)
+                auto g_at = [&](int l) {
+                    const int u = l / kPerThread;
+                    Partial<T> q;
+                    for (int r = u * kPerThread; r < l; ++r) q.add(s_d[r]);
+                    return delta * (s_S[u] + q.value());
+                };
+                const double inv_delta = 1.0 / delta;
+                for (int64_t i = i0 + t; i < i1; i += kDesignThreads) {
+                    const double tau = (double)i * GM / (double)N;
+                    int lo = 0, hi = U - 1;  // largest u with G at its first cell <= tau (u = 0 is)
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_G[mid] <= tau) lo = mid; else hi = mid - 1;
+                    }
+                    // largest cell r of thread lo with G_r <= tau: a candidate from
+                    // the running sums in T against tau / delta - S, then the exact
+                    // FP64 G of the candidate and its right neighbour decide
+                    const int nr = min(kPerThread, cnt - lo * kPerThread);
+                    const T target = (T)(tau * inv_delta - s_S[lo]);
+                    Partial<T> run;
+                    int r = 0;
+                    for (int q = 1; q < nr; ++q) {
+                        run.add(s_d[lo * kPerThread + q - 1]);
+                        if (approx(run) <= target) r = q;
+                    }
+                    int kl = lo * kPerThread + r;
+                    double Gk = g_at(kl);
+                    while (kl > lo * kPerThread && !(Gk <= tau)) Gk = g_at(--kl);
+                    while (kl + 1 < lo * kPerThread + nr) {
+                        const double Gn = g_at(kl + 1);
+                        if (!(Gn <= tau)) break;
+                        ++kl;
+                        Gk = Gn;
+                    }
+                    int kk = kl;  // largest cell <= kl of positive density
+                    while (kk >= 0 && !(s_d[kk] > T(0))) --kk;
+                    double x;
+                    if (kk >= 0) {
+                        if (kk != kl) Gk = g_at(kk);
+                        const double dk = (double)s_d[kk];
+                        x = __dadd_rn(a, __dmul_rn((double)(c0 + kk), delta));
+                        const double step = fmin(fmax((tau - Gk) / dk, 0.0), delta);
+                        x = __dadd_rn(x, step);
+                    } else if (lastpos >= 0) {
+                        // no density from cell lastpos + 1 to here, so tau is at or past
+                        // G at the end of cell lastpos: its right edge
+                        x = __dadd_rn(__dadd_rn(a, __dmul_rn((double)lastpos, delta)), delta);
+                    } else {
+                        x = a;  // no positive density from the start of I
+                    }
+                    knots[i] = x;
+                }
+            }
+            const int cl = clast[ch];
+            if (cl >= 0) lastpos = c0 + cl;
+            __syncthreads();  // s_d, s_S and s_range are rewritten for the next chunk
+        }
+    }
+}
+
+// ---- fused design, FP32 mode ------------------------------------------------
+// The FP32-density variant of design_fused_kernel, arranged so that almost
+// no FP64 operation is spent per density cell (GB300 runs about one FP64
+// operation per SM and cycle):
+//   - pass A writes the FP32 densities to scratch; pass B reads them back;
+//   - sums inside a chunk are float-float (a compensated pair hi + lo, about
+//     48 significant bits): thread partials, the block scan and the chunk
+//     total; the chunk totals, their scan and G_M are FP64;
+//   - the knot search compares float-float values in FP32, in units of the
+//     density sum (G / delta): the target tau_i / delta = i G_M / (N delta)
+//     minus the chunk base is formed in FP64 once per knot and split into a
+//     float-float pair;
+//   - the step inside the cell, (tau_i - G_k) / d_k, is FP32 (it is at most
+//     delta, so its rounding is below 1e-7 delta), and x = a + k delta + step
+//     is FP64.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF x, FF y)
+{
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float bp = __fsub_rn(s, x.hi);
+    const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bp)), __fsub_rn(y.hi, bp));
+    const float t = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+    const float hi = __fadd_rn(s, t);
+    return FF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
+__device__ __forceinline__ bool ff_le(FF x, FF y) { return x.hi < y.hi || (x.hi == y.hi && x.lo <= y.lo); }
+__device__ __forceinline__ FF ff_from_double(double v)
+{
+    const float hi = __double2float_rn(v);
+    return FF{hi, __double2float_rn(v - (double)hi)};
+}
+__device__ __forceinline__ double ff_to_double(FF x) { return (double)x.hi + (double)x.lo; }
+
+// Block-wide exclusive scan of one float-float per thread (kDesignThreads);
+// *total receives the block sum.
+__device__ __forceinline__ FF ff_block_exclusive_scan(FF v, FF* s_w, FF* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int W = kDesignThreads / 32;
+    FF incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const FF n{__shfl_up_sync(0xffffffffu, incl.hi, o), __shfl_up_sync(0xffffffffu, incl.lo, o)};
+        if (lane >= o) incl = ff_add(n, incl);
+    }
+    FF excl{__shfl_up_sync(0xffffffffu, incl.hi, 1), __shfl_up_sync(0xffffffffu, incl.lo, 1)};
+    if (lane == 0) excl = FF{0.0f, 0.0f};
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        FF ws = lane < W ? s_w[lane] : FF{0.0f, 0.0f};
+        FF wi = ws;
+        for (int o = 1; o < W; o <<= 1) {
+            const FF n{__shfl_up_sync(0xffffffffu, wi.hi, o), __shfl_up_sync(0xffffffffu, wi.lo, o)};
+            if (lane >= o) wi = ff_add(n, wi);
+        }
+        FF we{__shfl_up_sync(0xffffffffu, wi.hi, 1), __shfl_up_sync(0xffffffffu, wi.lo, 1)};
+        if (lane == 0) we = FF{0.0f, 0.0f};
+        if (lane < W) s_w[lane] = we;
+        if (lane == W - 1) s_w[W] = wi;
+    }
+    __syncthreads();
+    const FF r = ff_add(s_w[warp], excl);
+    *total = s_w[W];
+    __syncthreads();
+    return r;
+}
+
+// smallest i in [1, N] with i c >= S (N if none below N), c = G_M / (N delta)
+__device__ __forceinline__ int64_t first_target_at_or_above_units(double S, double c, int64_t N)
+{
+    const double e = floor(S / c);
+    int64_t i = (int64_t)fmin(fmax(e, 1.0), (double)N);
+    while (i > 1 && (double)(i - 1) * c >= S) --i;
+    while (i < N && (double)i * c < S) ++i;
+    return i;
+}
+
+__global__ void __launch_bounds__(kDesignThreads) design_fused_fp32_kernel(DesignPlan p)
+{
+    __shared__ float s_d[kChunk];
+    __shared__ FF s_ex[kDesignThreads];  // exclusive float-float prefix of the thread partials
+    __shared__ FF s_w[kDesignThreads / 32 + 1];
+    __shared__ double s_warp[kDesignThreads / 32 + 1];
+    __shared__ int s_last;
+    __shared__ int64_t s_range[2];
+    const int t = threadIdx.x;
+    float* __restrict__ dbuf_all = reinterpret_cast<float*>(p.d);
+    for (int o = blockIdx.x; o < p.F; o += gridDim.x) {
+        const int f = p.order[o];
+        const pwl_func F = p.funcs[f];
+        const int64_t M = p.moff[f + 1] - p.moff[f];
+        const int64_t N = p.koff[f + 1] - p.koff[f] - 1;
+        const int64_t nch = p.choff[f + 1] - p.choff[f];
+        const double a = F.a, b = F.b;
+        const double delta = (b - a) / (double)M;
+        const float deltaf = (float)delta;
+        double* __restrict__ knots = p.knots + p.koff[f];
+        double* __restrict__ csum = p.csum + p.choff[f];
+        double* __restrict__ cbase = p.cbase + p.choff[f];
+        int* __restrict__ clast = p.clast + p.choff[f];
+        float* __restrict__ dbuf = dbuf_all + p.moff[f];
+
+        // pass A: densities (to scratch), chunk totals, last positive cell
+        for (int64_t ch = 0; ch < nch; ++ch) {
+            const int64_t c0 = ch * kChunk;
+            const int cnt = (int)min((int64_t)kChunk, M - c0);
+            const float t0f = (float)(a + (double)c0 * delta);
+            FF part{0.0f, 0.0f};
+            int last = -1;
+            for (int r = 0; r < kPerThread; ++r) {
+                const int l = t * kPerThread + r;
+                if (l < cnt) {
+                    const float dk = fused_density<float>(F, a, delta, c0 + l, t0f, deltaf, l);
+                    dbuf[c0 + l] = dk;
+                    part = ff_add(part, FF{dk, 0.0f});
+                    if (dk > 0.0f) last = l;
+                }
+            }
+            if (t == 0) s_last = -1;
+            __syncthreads();
+            if (last >= 0) atomicMax(&s_last, last);
+            FF tot;
+            ff_block_exclusive_scan(part, s_w, &tot);
+            if (t == 0) {
+                csum[ch] = ff_to_double(tot);
+                clast[ch] = s_last;
+            }
+        }
+        __syncthreads();
+        double carry = 0.0;
+        for (int64_t base = 0; base < nch; base += kDesignThreads) {
+            const int64_t c = base + t;
+            const double v = c < nch ? csum[c] : 0.0;
+            double tot;
+            const double ex = block_exclusive_scan(v, s_warp, &tot);
+            if (c < nch) cbase[c] = carry + ex;
+            carry += tot;
+        }
+        __syncthreads();
+        const double GM = delta * carry;
+        if (t == 0) {
+            knots[0] = a;
+            knots[N] = b;
+        }
+        if (!(GM > 0.0)) {
+            for (int64_t i = 1 + t; i < N; i += kDesignThreads) knots[i] = a + (double)i * (b - a) / (double)N;
+            __syncthreads();
+            continue;
+        }
+        const double cunit = carry / (double)N;  // tau_i / delta = i * cunit
+
+        // pass B
+        int64_t lastpos = -1;
+        for (int64_t ch = 0; ch < nch; ++ch) {
+            const int64_t c0 = ch * kChunk;
+            if (t == 0) {
+                s_range[0] = first_target_at_or_above_units(cbase[ch], cunit, N);
+                s_range[1] = ch + 1 < nch ? first_target_at_or_above_units(cbase[ch + 1], cunit, N) : N;
+            }
+            __syncthreads();
+            const int64_t i0 = s_range[0], i1 = s_range[1];
+            if (i0 < i1) {
+                const int cnt = (int)min((int64_t)kChunk, M - c0);
+                FF part{0.0f, 0.0f};
+                for (int r = 0; r < kPerThread; ++r) {
+                    const int l = t * kPerThread + r;
+                    if (l < cnt) {
+                        const float dk = dbuf[c0 + l];
+                        s_d[l] = dk;
+                        part = ff_add(part, FF{dk, 0.0f});
+                    }
+                }
+                FF tot;
+                s_ex[t] = ff_block_exclusive_scan(part, s_w, &tot);
+                __syncthreads();
+                const int U = (cnt + kPerThread - 1) / kPerThread;
+                const double cb = cbase[ch];
+                // float-float prefix of local cell l: S_u + the thread's cells before l
+                auto ff_at = [&](int l) {
+                    const int u = l / kPerThread;
+                    FF q = s_ex[u];
+                    for (int r = u * kPerThread; r < l; ++r) q = ff_add(q, FF{s_d[r], 0.0f});
+                    return q;
+                };
+                for (int64_t i = i0 + t; i < i1; i += kDesignThreads) {
+                    const FF tl = ff_from_double((double)i * cunit - cb);  // target in the chunk
+                    int lo = 0, hi = U - 1;  // largest u with S_u <= target (u = 0 is)
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (ff_le(s_ex[mid], tl)) lo = mid; else hi = mid - 1;
+                    }
+                    const int nr = min(kPerThread, cnt - lo * kPerThread);
+                    FF q = s_ex[lo], Sk = q;
+                    int kl = lo * kPerThread;
+                    for (int r = 1; r < nr; ++r) {
+                        q = ff_add(q, FF{s_d[lo * kPerThread + r - 1], 0.0f});
+                        if (!ff_le(q, tl)) break;
+                        kl = lo * kPerThread + r;
+                        Sk = q;
+                    }
+                    int kk = kl;
+                    while (kk >= 0 && !(s_d[kk] > 0.0f)) --kk;
+                    double x;
+                    if (kk >= 0) {
+                        if (kk != kl) Sk = ff_at(kk);
+                        const FF diff = ff_add(tl, ff_neg(Sk));  // (tau - G_k) / delta
+                        const float step = fminf(fmaxf((diff.hi + diff.lo) * deltaf / s_d[kk], 0.0f), deltaf);
+                        x = __dadd_rn(__fma_rn((double)(c0 + kk), delta, a), (double)step);
+                    } else if (lastpos >= 0) {
+                        x = __dadd_rn(__dadd_rn(a, __dmul_rn((double)lastpos, delta)), delta);
+                    } else {
+                        x = a;
+                    }
+                    knots[i] = x;
+                }
+            }
+            const int cl = clast[ch];
+            if (cl >= 0) lastpos = c0 + cl;
+            __syncthreads();
+        }
+    }
+}
+
 // Writes the descriptor and offsets of a one-function batch into the
 // workspace (kernel parameters, so the call needs no host-to-device copy).
 __global__ void single_setup_kernel(pwl_func F, int64_t N, int64_t M, pwl_func* funcs,
@@ -262,6 +722,18 @@ pwl_status design_launch(const DesignPlan& p, cudaStream_t s)
     const int grid_knots = (int)std::min<int64_t>((p.total_knots + 255) / 256, (int64_t)di.sms * 16);
     invert_kernel<<<grid_knots, 256, 0, s>>>(p);
     PWL_CHECK_LAUNCH("invert_kernel");
+    return PWL_OK;
+}
+
+pwl_status design_fused_launch(const DesignPlan& p, cudaStream_t s)
+{
+    const DeviceInfo& di = device_info();
+    const int grid = (int)std::min<int64_t>(p.F, (int64_t)di.sms * 8);
+    if (p.precision == PWL_PREC_FP32)
+        design_fused_fp32_kernel<<<grid, kDesignThreads, 0, s>>>(p);
+    else
+        design_fused_kernel<double><<<grid, kDesignThreads, 0, s>>>(p);
+    PWL_CHECK_LAUNCH("design_fused_kernel");
     return PWL_OK;
 }
 

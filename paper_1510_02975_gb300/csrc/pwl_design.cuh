@@ -25,12 +25,19 @@ struct DesignPlan {
     double* cbase;  // total_chunks exclusive chunk bases
     double* stot;   // F totals (sum of d over the function)
     double* knots;  // total_knots output
+    // fused per-function path (batches)
+    const int* order;  // F function indices, largest M first
+    int* clast;        // total_chunks: last cell of positive density in the chunk (local index), or -1;
+                       // must not overlap d (the FP32 fused kernel keeps FP32 densities there)
 };
 
 int64_t design_chunks(int64_t M);
 size_t design_scratch_bytes(int64_t F, int64_t total_cells, int64_t total_chunks);
 void design_carve_scratch(DesignPlan& p, void* scratch);
 pwl_status design_launch(const DesignPlan& p, cudaStream_t s);
+// One persistent launch for a batch: each CTA designs whole functions (in
+// p.order); needs p.order and p.clast, writes p.csum, p.cbase and p.knots.
+pwl_status design_fused_launch(const DesignPlan& p, cudaStream_t s);
 
 // Projection: F functions with knots at koff (device), values out.
 struct ProjectPlan {
@@ -46,12 +53,16 @@ struct ProjectPlan {
     double* values;
     double2* lr;           // per interval: (int f phi_left, int f phi_right)
     double* cr;            // 4 * total_knots doubles of solver scratch (used when rows do not fit smem)
+    int solver;            // 0: cyclic reduction, one CTA per function; 1: Thomas, one thread per function
 };
 
 struct GaussLegendre {
     int Q;
-    double x[16];
-    double w[16];
+    double x[16];   // nodes on [-1, 1]
+    double w[16];   // weights
+    double wl[16];  // w (1 - x) / 2: the weight times the left hat phi_{j-1} at the node
+    double wr[16];  // w (1 + x) / 2: the weight times the right hat phi_j at the node
+    float xf[16];   // nodes rounded to FP32
 };
 const GaussLegendre& gauss_legendre_rule(int Q);
 

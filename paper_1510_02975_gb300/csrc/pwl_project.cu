@@ -57,6 +57,12 @@ __global__ void interp_values_kernel(ProjectPlan p)
 }
 
 // (L_j, R_j) = (int_{I_j} f phi_{j-1}, int_{I_j} f phi_j) for every interval.
+// At the node t_q = mid + half x_q the hats are phi_{j-1} = (1 - x_q)/2 and
+// phi_j = (1 + x_q)/2, so L_j = half sum_q wl_q f(t_q) and
+// R_j = half sum_q wr_q f(t_q) with the host-side weights wl, wr: no
+// division per node.  FP64 mode: t_q and the sums in FP64.  FP32 mode: t_q
+// and f(t_q) in FP32 (the argument of an FP32 f is rounded to FP32 anyway),
+// the sums in FP64.
 template <typename T>
 __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ GaussLegendre gl)
 {
@@ -67,17 +73,71 @@ __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ Gaus
         const int64_t j = g - (p.koff[f] - f) + 1;  // interval index 1..N_f
         const double* x = p.knots + p.koff[f];
         const double xl = x[j - 1], xr = x[j];
-        const double h = xr - xl;
-        const double mid = 0.5 * (xl + xr), half = 0.5 * h;
+        const double mid = 0.5 * (xl + xr), half = 0.5 * (xr - xl);
         const pwl_func F = p.funcs[f];
         double L = 0.0, R = 0.0;
-        for (int q = 0; q < gl.Q; ++q) {
-            const double t = __dadd_rn(mid, __dmul_rn(half, gl.x[q]));
-            const double fw = __dmul_rn(__dmul_rn(half, gl.w[q]), (double)func_value<T>(F, (T)t));
-            L = L + fw * (xr - t) / h;
-            R = R + fw * (t - xl) / h;
+        if constexpr (sizeof(T) == 4) {
+            const float midf = (float)mid, halff = (float)half;
+            for (int q = 0; q < gl.Q; ++q) {
+                const double fv = (double)func_value<float>(F, __fmaf_rn(halff, gl.xf[q], midf));
+                L = __fma_rn(gl.wl[q], fv, L);
+                R = __fma_rn(gl.wr[q], fv, R);
+            }
+        } else {
+            for (int q = 0; q < gl.Q; ++q) {
+                const double fv = func_value<double>(F, __fma_rn(half, gl.x[q], mid));
+                L = __fma_rn(gl.wl[q], fv, L);
+                R = __fma_rn(gl.wr[q], fv, R);
+            }
         }
-        p.lr[g] = make_double2(L, R);
+        p.lr[g] = make_double2(half * L, half * R);
+    }
+}
+
+// Gram system of a batch of functions, one thread per function: the
+// Thomas algorithm (forward elimination, back substitution) in FP64, the
+// rows assembled on the fly (M_{i,i-1} = h_i/6, M_ii = (h_i + h_{i+1})/3,
+// M_{i,i+1} = h_{i+1}/6, b_i = R_i + L_{i+1}).  O(N) operations per
+// function and no barriers: the right solver when thousands of functions
+// run at once; the forward multipliers go to scratch, the values array
+// holds the eliminated right-hand side until back substitution.
+__global__ void gram_thomas_kernel(ProjectPlan p)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < p.F; f += stride) {
+        const int64_t k0 = p.koff[f];
+        const int n = (int)(p.koff[f + 1] - k0);
+        const int N = n - 1;
+        const double* x = p.knots + k0;
+        const double2* lr = p.lr + (k0 - f);
+        double* cp = p.cr + 4 * k0;  // forward multipliers c'_i
+        double* dv = p.values + k0;  // d'_i, then the solution
+        constexpr double kSixth = 1.0 / 6.0, kThird = 1.0 / 3.0;
+        double xm = x[0], x0 = x[0], x1 = N >= 1 ? x[1] : x[0];
+        double cprev = 0.0, dprev = 0.0;
+        double2 lprev = make_double2(0.0, 0.0);
+        for (int i = 0; i < n; ++i) {
+            const double hl = i > 0 ? x0 - xm : 0.0;
+            const double hr = i < N ? x1 - x0 : 0.0;
+            const double2 lri = i < N ? lr[i] : make_double2(0.0, 0.0);
+            const double rhs = lprev.y + lri.x;
+            const double lower = hl * kSixth;
+            const double denom = (hl + hr) * kThird - lower * cprev;
+            const double r = 1.0 / denom;
+            cprev = (i < N) ? hr * kSixth * r : 0.0;
+            dprev = (rhs - lower * dprev) * r;
+            cp[i] = cprev;
+            dv[i] = dprev;
+            lprev = lri;
+            xm = x0;
+            x0 = x1;
+            x1 = (i + 2 <= N) ? x[i + 2] : x1;
+        }
+        double v = dv[N];
+        for (int i = N - 1; i >= 0; --i) {
+            v = dv[i] - cp[i] * v;
+            dv[i] = v;
+        }
     }
 }
 
@@ -206,6 +266,11 @@ const GaussLegendre& gauss_legendre_rule(int Q)
         for (int q = 1; q <= 16; ++q) {
             rules[q].Q = q;
             legendre_rule(q, rules[q].x, rules[q].w);
+            for (int i = 0; i < q; ++i) {
+                rules[q].wl[i] = rules[q].w[i] * (1.0 - rules[q].x[i]) * 0.5;
+                rules[q].wr[i] = rules[q].w[i] * (1.0 + rules[q].x[i]) * 0.5;
+                rules[q].xf[i] = (float)rules[q].x[i];
+            }
         }
     });
     return rules[Q];
@@ -243,6 +308,12 @@ pwl_status project_launch(const ProjectPlan& p, const GaussLegendre& gl, cudaStr
     else
         hat_integrals_kernel<double><<<grid, 128, 0, s>>>(p, gl);
     PWL_CHECK_LAUNCH("hat_integrals_kernel");
+    if (p.solver == 1) {
+        const int grid_t = (int)std::min<int64_t>((p.F + 63) / 64, (int64_t)di.sms * 16);
+        gram_thomas_kernel<<<grid_t, 64, 0, s>>>(p);
+        PWL_CHECK_LAUNCH("gram_thomas_kernel");
+        return PWL_OK;
+    }
     const size_t smem = sizeof(double) * 4 * (size_t)p.max_rows;
     const int use_smem = smem <= di.smem_optin ? 1 : 0;
     if (use_smem) {

@@ -79,6 +79,25 @@ def batch_functions(n_funcs: int = 4096, seed: int = 3, knots_lo: int = 16, knot
     return funcs, n_int, n_q
 
 
+def batch_queries(funcs, n_q, seed: int = 6, device="cuda"):
+    """Concatenated float32 queries of a batch: function f's n_q[f] queries,
+    uniform on its domain [a_f, b_f), follow those of functions 0..f-1.
+    Returns (x, offsets) with offsets a list of F+1 ints."""
+    import torch
+    offsets = [0]
+    for n in n_q:
+        offsets.append(offsets[-1] + int(n))
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    x = torch.rand(offsets[-1], generator=g, device=device, dtype=torch.float32)
+    counts = torch.tensor([int(n) for n in n_q], device=device)
+    a = torch.tensor([float(f["a"]) for f in funcs], device=device, dtype=torch.float32)
+    w = torch.tensor([float(f["b"] - f["a"]) for f in funcs], device=device, dtype=torch.float32)
+    x.mul_(torch.repeat_interleave(w, counts, output_size=offsets[-1]))
+    x.add_(torch.repeat_interleave(a, counts, output_size=offsets[-1]))
+    return x, offsets
+
+
 def channel_inputs(rows: int, channels: int, seed: int = 4, sigma: float = 2.0, device="cuda"):
     """x[rows, channels] float32 normal(0, sigma) for the channel-wise map."""
     import torch
