@@ -248,8 +248,8 @@ pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, f
  *   m_per_interval density cells per interval of the design step
  *                  (M_f = m_per_interval N_f); 0 selects 64
  *   cells_per_knot cells of each function's evaluation index per knot
- *                  (0 selects 4), reduced where the index would not leave
- *                  room for two CTAs per SM
+ *                  (0 selects 4), reduced where the index would not fit one
+ *                  CTA's shared memory
  * Allocates all device memory of the batch (synchronously); the batch owns
  * it until pwl_batch_destroy.  Errors: PWL_EINVAL (sizes, a descriptor),
  * PWL_ENOMEM / PWL_ECUDA (allocation).                                      */
@@ -289,13 +289,19 @@ pwl_status pwl_batch_check(pwl_batch b, void* stream);
  * share of the function's queries times stage_min is at least the index
  * bytes (stage_min 0: never stage; -1: keep the current value, initially
  * 16).  shape (-1 keeps the current one, initially 0):
- *   0  one 1024-thread CTA per SM with two record buffers: a bulk copy
- *      (cp.async.bulk) brings the next piece's records while the CTA
- *      streams the current piece;
- *   1  one 1024-thread CTA per SM, staging by the CTA's threads;
- *   2  two 512-thread CTAs per SM, staging by the CTA's threads;
+ *   0  one 1024-thread CTA per SM staging the records with its threads (an
+ *      index of up to all of the CTA's shared memory);
+ *   1  as 0, the queries streamed through a 4-slot cp.async ring in shared
+ *      memory (the index gets the rest);
+ *   2  two 512-thread CTAs per SM, each staging with its threads (an index
+ *      of up to half of the SM's shared memory);
  *   3  no staging: every piece reads its records through L1 (stage_min is
- *      ignored).
+ *      ignored);
+ *   4  one 1024-thread CTA per SM with two record buffers: a bulk copy
+ *      (cp.async.bulk) brings the next piece's records while the CTA
+ *      streams the current piece (an index of up to half of the CTA's
+ *      shared memory).
+ * A function whose index exceeds the shape's budget is read through L1.
  * Allocates the plan (synchronously; the previous plan is freed).  A wait
  * for a bulk copy gives up after 1 s; pwl_batch_check then reports
  * PWL_ETIMEOUT.                                                             */
@@ -308,9 +314,9 @@ pwl_status pwl_batch_plan(pwl_batch b, const int64_t* query_offsets, int32_t sha
 pwl_status pwl_batch_eval(pwl_batch b, const float* d_x, float* d_y, void* stream);
 
 /* Autotuner: times pwl_batch_eval on the caller's x and y (reps timed
- * launches per candidate after one warm-up) for every CTA shape (0..3) and
+ * launches per candidate after one warm-up) for every CTA shape (0..4) and
  * staging threshold stage_min in {0, 4, 16, 64}, and keeps the fastest plan.
- * timings_ms: host array of 16 floats receiving the mean launch time of
+ * timings_ms: host array of 20 floats receiving the mean launch time of
  * candidate (shape, threshold) at index 4 shape + threshold position, or
  * NULL.  Writes y; synchronizes `stream`; must not run during stream
  * capture.                                                                  */

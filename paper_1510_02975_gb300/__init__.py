@@ -266,11 +266,11 @@ def pwl_batch_autotune(handle, x, y, reps: int = 3, stream=None) -> dict:
     if x.numel() < planned:
         raise ValueError(f"x has {x.numel()} elements; the plan has {planned} queries")
     _require(y, torch.float32, "y", x.numel())
-    t = (ctypes.c_float * 16)()
+    t = (ctypes.c_float * 20)()
     check(load().pwl_batch_autotune(ctypes.c_void_p(handle), _ptr(x), _ptr(y), reps, t, _stream(stream)),
           "pwl_batch_autotune")
     return {(shape, stage_min): float(t[4 * shape + j])
-            for shape in range(4) for j, stage_min in enumerate((0, 4, 16, 64))}
+            for shape in range(5) for j, stage_min in enumerate((0, 4, 16, 64))}
 
 
 def pwl_batch_get_info(handle) -> dict:

@@ -432,25 +432,31 @@ __global__ void __launch_bounds__(1024, 1) batch_eval_async_kernel(const EvalPar
 }
 
 // Launch shapes the planner and the autotuner choose from.  All keep <= 64
-// registers per thread (1024 threads per SM).
+// registers per thread (1024 threads per SM).  A shape stages a function's
+// index only if it fits the shape's staging budget: the shared memory one of
+// its CTAs gets (ctas per SM) minus the ring.
 using BatchEvalKernel = void (*)(const EvalParams, const float*, float*);
 enum StageKind { kStageAsync = 0, kStageSync = 1, kStageNone = 2 };
 constexpr int kRingDepth = 4;
 struct EvalShape {
     int threads;
+    int ctas;   // CTAs per SM the shape is meant to run
     int stage;  // StageKind
     int ring;   // cp.async ring depth (0: vectors in registers)
     BatchEvalKernel kern;
 };
 const EvalShape kShapes[] = {
-    // 1 CTA / SM, two record buffers filled by bulk copies, 4 vectors in registers
-    {1024, kStageAsync, 0, batch_eval_async_kernel<4>},
+    // 1 CTA / SM, records staged by the CTA (up to all of its shared memory),
+    // 4 query vectors in registers
+    {1024, 1, kStageSync, 0, batch_eval_kernel<1024, 1, 4, 0, 0>},
     // 1 CTA / SM, records staged by the CTA, queries through a 4-slot ring
-    {1024, kStageSync, kRingDepth, batch_eval_kernel<1024, 1, 4, 0, kRingDepth>},
+    {1024, 1, kStageSync, kRingDepth, batch_eval_kernel<1024, 1, 4, 0, kRingDepth>},
     // 2 CTAs / SM, records staged by the CTA, 4 vectors in registers
-    {512, kStageSync, 0, batch_eval_kernel<512, 2, 4, 0, 0>},
+    {512, 2, kStageSync, 0, batch_eval_kernel<512, 2, 4, 0, 0>},
     // 1 CTA / SM, records through L1, queries through a 4-slot ring
-    {1024, kStageNone, kRingDepth, batch_eval_kernel<1024, 1, 4, 1, kRingDepth>},
+    {1024, 1, kStageNone, kRingDepth, batch_eval_kernel<1024, 1, 4, 1, kRingDepth>},
+    // 1 CTA / SM, two record buffers filled by bulk copies, 4 vectors in registers
+    {1024, 1, kStageAsync, 0, batch_eval_async_kernel<4>},
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -526,12 +532,12 @@ constexpr double kPieceCost = 65536.0;
 constexpr double kQueryCost = 8.0;
 constexpr double kDirectQueryCost = 24.0;
 
-void make_plan(const pwl_batch_s* b, const int64_t* qo, int G, int64_t stage_min, std::vector<WorkItem>& items,
-               std::vector<int>& range)
+void make_plan(const pwl_batch_s* b, const int64_t* qo, int G, int64_t stage_min, size_t budget,
+               std::vector<WorkItem>& items, std::vector<int>& range)
 {
     auto staged_piece = [&](int64_t f, int64_t nq) {
         const size_t ib = index_bytes(b, f);
-        return stage_min > 0 && ib <= b->index_budget && (size_t)nq * (size_t)stage_min >= ib;
+        return stage_min > 0 && ib <= budget && (size_t)nq * (size_t)stage_min >= ib;
     };
     auto cost = [&](int64_t f, int64_t nq) {
         const bool st = staged_piece(f, nq);
@@ -622,8 +628,8 @@ pwl_status pwl_batch_create(const pwl_func* funcs, const int64_t* n_intervals, i
     b->N.assign(n_intervals, n_intervals + n_funcs);
     b->koff.resize(n_funcs + 1);
     b->K.resize(n_funcs);
-    // two CTAs per SM, each staging at most half of the SM's shared memory
-    b->index_budget = std::min(di.smem_optin, di.smem_per_sm / 2 - 1024);
+    // the largest index one CTA can stage (shape 0: one CTA per SM)
+    b->index_budget = di.smem_optin - 1024;
     std::vector<int64_t> moff(n_funcs + 1), choff(n_funcs + 1);
     std::vector<BatchFunc> bfh(n_funcs);
     b->koff[0] = moff[0] = choff[0] = 0;
@@ -761,7 +767,10 @@ pwl_status pwl_batch_project(pwl_batch b, int32_t form, int32_t quad_points, int
     p.knots = b->knots;
     p.values = b->values;
     project_carve_scratch(p, b->project_scratch);
-    p.solver = 0;  // cyclic reduction, one CTA per function
+    // many functions: one warp each (partitioned Thomas); few: one CTA each
+    // (cyclic reduction)
+    p.solver = b->F >= 64 ? 1 : 0;
+    p.order = b->order;
     return project_launch(p, gauss_legendre_rule(quad_points), as_stream(stream));
 }
 
@@ -810,19 +819,27 @@ pwl_status pwl_batch_plan(pwl_batch b, const int64_t* query_offsets, int32_t sha
     if (stage_min < 0) stage_min = b->stage_min;
     const EvalShape& sh = kShapes[shape];
     if (sh.stage == kStageNone) stage_min = 0;
+    // staging budget of one buffer: the CTA's share of the SM's shared memory
+    // minus the ring (and halved for two buffers)
+    const DeviceInfo& di = device_info();
+    const size_t ring = (size_t)sh.ring * 16 * (size_t)sh.threads;
+    const size_t cta_smem = std::min(di.smem_optin, di.smem_per_sm / (size_t)sh.ctas - 1024);
+    size_t budget = cta_smem > ring + 1024 ? cta_smem - ring - 1024 : 0;
+    if (sh.stage == kStageAsync) budget /= 2;
+    if (sh.stage == kStageNone) budget = 0;
+    budget &= ~(size_t)15;
     size_t buf = 0;  // bytes of the largest index that may be staged
     for (int64_t f = 0; f < b->F; ++f) {
         const size_t ib = index_bytes(b, f);
-        if (ib <= b->index_budget) buf = std::max(buf, ib);
+        if (ib <= budget) buf = std::max(buf, ib);
     }
     buf = (buf + 15) & ~(size_t)15;
-    const size_t ring = (size_t)sh.ring * 16 * (size_t)sh.threads;
     const size_t smem = (sh.stage == kStageAsync ? 2 * buf : (sh.stage == kStageSync ? buf : 0)) + ring;
     int grid = 0;
     PWL_CUDA_TRY(occupancy_grid(sh.kern, sh.threads, smem, &grid));
     std::vector<WorkItem> items;
     std::vector<int> range;
-    make_plan(b, query_offsets, grid, stage_min, items, range);
+    make_plan(b, query_offsets, grid, stage_min, budget, items, range);
     void* dev = nullptr;
     const size_t bytes_items = align256(sizeof(WorkItem) * std::max<size_t>(items.size(), 1));
     PWL_CUDA_TRY(cudaMalloc(&dev, bytes_items + sizeof(int) * (size_t)(grid + 1)));

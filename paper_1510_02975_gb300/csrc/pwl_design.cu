@@ -262,7 +262,10 @@ __device__ __forceinline__ float fused_density<float>(const pwl_func& F, double,
                                                       float deltaf, int local)
 {
     const float t = __fmaf_rn((float)local + 0.5f, deltaf, t0f);
-    return powf(fabsf(func_second_derivative<float>(F, t)), 0.4f);
+    // |f''|^{2/5} by the hardware exp2/log2 pair (__powf): a few ulp, far
+    // below what the FP32 density mode promises (knots within 1e-3 of the
+    // shortest interval), for a third of the instructions of powf
+    return __powf(fabsf(func_second_derivative<float>(F, t)), 0.4f);
 }
 
 // smallest i in [1, N] with tau_i = i G_M / N >= G (N if none below N)
@@ -507,6 +510,21 @@ __device__ __forceinline__ FF ff_block_exclusive_scan(FF v, FF* s_w, FF* total)
     return r;
 }
 
+// Block-wide float-float sum (kDesignThreads); the result is valid in
+// thread 0.  One barrier.
+__device__ __forceinline__ FF ff_block_sum(FF v, FF* s_w)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_add(v, FF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
+    if (lane == 0) s_w[warp] = v;
+    __syncthreads();
+    FF r{0.0f, 0.0f};
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kDesignThreads / 32; ++w) r = ff_add(r, s_w[w]);
+    return r;
+}
+
 // smallest i in [1, N] with i c >= S (N if none below N), c = G_M / (N delta)
 __device__ __forceinline__ int64_t first_target_at_or_above_units(double S, double c, int64_t N)
 {
@@ -517,16 +535,19 @@ __device__ __forceinline__ int64_t first_target_at_or_above_units(double S, doub
     return i;
 }
 
-__global__ void __launch_bounds__(kDesignThreads) design_fused_fp32_kernel(DesignPlan p)
+__global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(DesignPlan p)
 {
     __shared__ float s_d[kChunk];
     __shared__ FF s_ex[kDesignThreads];  // exclusive float-float prefix of the thread partials
-    __shared__ FF s_w[kDesignThreads / 32 + 1];
+    __shared__ FF s_w[2 * (kDesignThreads / 32) + 1];
+    __shared__ int s_last2[2];
     __shared__ double s_warp[kDesignThreads / 32 + 1];
     __shared__ int s_last;
     __shared__ int64_t s_range[2];
     const int t = threadIdx.x;
     float* __restrict__ dbuf_all = reinterpret_cast<float*>(p.d);
+    if (t < 2) s_last2[t] = -1;
+    __syncthreads();
     for (int o = blockIdx.x; o < p.F; o += gridDim.x) {
         const int f = p.order[o];
         const pwl_func F = p.funcs[f];
@@ -558,14 +579,16 @@ __global__ void __launch_bounds__(kDesignThreads) design_fused_fp32_kernel(Desig
                     if (dk > 0.0f) last = l;
                 }
             }
-            if (t == 0) s_last = -1;
-            __syncthreads();
-            if (last >= 0) atomicMax(&s_last, last);
-            FF tot;
-            ff_block_exclusive_scan(part, s_w, &tot);
+            // chunk total and last positive cell: one barrier per chunk (the
+            // slot pair alternates so that a chunk's writes never meet the
+            // previous chunk's reads)
+            const int slot = (int)(ch & 1);
+            if (last >= 0) atomicMax(&s_last2[slot], last);
+            const FF tot = ff_block_sum(part, s_w + slot * (kDesignThreads / 32));
             if (t == 0) {
                 csum[ch] = ff_to_double(tot);
-                clast[ch] = s_last;
+                clast[ch] = s_last2[slot];
+                s_last2[slot] = -1;
             }
         }
         __syncthreads();

@@ -53,7 +53,8 @@ struct ProjectPlan {
     double* values;
     double2* lr;           // per interval: (int f phi_left, int f phi_right)
     double* cr;            // 4 * total_knots doubles of solver scratch (used when rows do not fit smem)
-    int solver;            // 0: cyclic reduction, one CTA per function; 1: Thomas, one thread per function
+    int solver;            // 0: cyclic reduction, one CTA per function; 1: partitioned Thomas, one warp per function
+    const int* order;      // solver 1: the order in which warps take the functions (NULL: 0..F-1)
 };
 
 struct GaussLegendre {
@@ -63,6 +64,7 @@ struct GaussLegendre {
     double wl[16];  // w (1 - x) / 2: the weight times the left hat phi_{j-1} at the node
     double wr[16];  // w (1 + x) / 2: the weight times the right hat phi_j at the node
     float xf[16];   // nodes rounded to FP32
+    float wlh[16], wll[16], wrh[16], wrl[16];  // wl, wr split into FP32 pairs hi + lo
 };
 const GaussLegendre& gauss_legendre_rule(int Q);
 

@@ -77,12 +77,27 @@ __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ Gaus
         const pwl_func F = p.funcs[f];
         double L = 0.0, R = 0.0;
         if constexpr (sizeof(T) == 4) {
+            // sums of w f(t) as float-float pairs: each product exact (the
+            // weight split hi + lo, the rounding error of hi f recovered by an
+            // FMA), each addition compensated; FP64 once per interval
             const float midf = (float)mid, halff = (float)half;
+            float Lh = 0.0f, Ll = 0.0f, Rh = 0.0f, Rl = 0.0f;
+            auto acc = [](float& h, float& l, float wh, float wlo, float fv) {
+                const float p = __fmul_rn(wh, fv);
+                const float pe = __fmaf_rn(wh, fv, -p) + __fmul_rn(wlo, fv);  // hi f - p exactly, plus lo f
+                const float s = __fadd_rn(h, p);
+                const float bp = __fsub_rn(s, h);
+                const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+                h = s;
+                l = __fadd_rn(l, __fadd_rn(e, pe));
+            };
             for (int q = 0; q < gl.Q; ++q) {
-                const double fv = (double)func_value<float>(F, __fmaf_rn(halff, gl.xf[q], midf));
-                L = __fma_rn(gl.wl[q], fv, L);
-                R = __fma_rn(gl.wr[q], fv, R);
+                const float fv = func_value<float>(F, __fmaf_rn(halff, gl.xf[q], midf));
+                acc(Lh, Ll, gl.wlh[q], gl.wll[q], fv);
+                acc(Rh, Rl, gl.wrh[q], gl.wrl[q], fv);
             }
+            L = (double)Lh + (double)Ll;
+            R = (double)Rh + (double)Rl;
         } else {
             for (int q = 0; q < gl.Q; ++q) {
                 const double fv = func_value<double>(F, __fma_rn(half, gl.x[q], mid));
@@ -94,49 +109,128 @@ __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ Gaus
     }
 }
 
-// Gram system of a batch of functions, one thread per function: the
-// Thomas algorithm (forward elimination, back substitution) in FP64, the
-// rows assembled on the fly (M_{i,i-1} = h_i/6, M_ii = (h_i + h_{i+1})/3,
-// M_{i,i+1} = h_{i+1}/6, b_i = R_i + L_{i+1}).  O(N) operations per
-// function and no barriers: the right solver when thousands of functions
-// run at once; the forward multipliers go to scratch, the values array
-// holds the eliminated right-hand side until back substitution.
-__global__ void gram_thomas_kernel(ProjectPlan p)
+// Gram system of a batch of functions, one warp per function, by a
+// partitioned Thomas algorithm (the SPIKE decomposition):
+//  1. lane p owns rows r0_p .. r1_p - 1 (m >= 2 rows; P <= 32 segments) and
+//     runs the Thomas elimination of its block with three right-hand sides:
+//     the load vector (solution y), the coupling a_{r0} e_0 to the unknown
+//     before the block (spike v) and the coupling c_{r1-1} e_{m-1} to the
+//     unknown after it (spike w), so that on the block x = y - v L_{p-1}
+//     - w F_{p+1}, with F_p, L_p the block's first and last unknowns;
+//  2. the 2P boundary unknowns follow from the first and last rows of every
+//     block: with L_{p-1} = alpha_{p-1} + beta_{p-1} F_p eliminated forward,
+//     F_p = gamma_p + delta_p F_{p+1}, then F and L backward from F_P = 0
+//     (a 2P-step recurrence in lane order, FP64; the spikes are below 1 in
+//     magnitude on this diagonally dominant matrix, so every pivot
+//     1 + v0_p beta_{p-1} stays near 1);
+//  3. every lane reconstructs its rows.
+// The rows are assembled on the fly (M_{i,i-1} = h_i/6, M_ii = (h_i +
+// h_{i+1})/3, M_{i,i+1} = h_{i+1}/6, b_i = R_i + L_{i+1}).  About 20 FP64
+// operations per row, one division; no barrier beyond the warp.
+__global__ void __launch_bounds__(64) gram_spike_kernel(ProjectPlan p, const int* __restrict__ order)
 {
-    const int stride = gridDim.x * blockDim.x;
-    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < p.F; f += stride) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    constexpr double kSixth = 1.0 / 6.0, kThird = 1.0 / 3.0;
+    for (int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); o < p.F; o += warps) {
+        const int f = order ? order[o] : o;
         const int64_t k0 = p.koff[f];
         const int n = (int)(p.koff[f + 1] - k0);
         const int N = n - 1;
-        const double* x = p.knots + k0;
-        const double2* lr = p.lr + (k0 - f);
-        double* cp = p.cr + 4 * k0;  // forward multipliers c'_i
-        double* dv = p.values + k0;  // d'_i, then the solution
-        constexpr double kSixth = 1.0 / 6.0, kThird = 1.0 / 3.0;
-        double xm = x[0], x0 = x[0], x1 = N >= 1 ? x[1] : x[0];
-        double cprev = 0.0, dprev = 0.0;
-        double2 lprev = make_double2(0.0, 0.0);
-        for (int i = 0; i < n; ++i) {
-            const double hl = i > 0 ? x0 - xm : 0.0;
-            const double hr = i < N ? x1 - x0 : 0.0;
-            const double2 lri = i < N ? lr[i] : make_double2(0.0, 0.0);
-            const double rhs = lprev.y + lri.x;
-            const double lower = hl * kSixth;
-            const double denom = (hl + hr) * kThird - lower * cprev;
-            const double r = 1.0 / denom;
-            cprev = (i < N) ? hr * kSixth * r : 0.0;
-            dprev = (rhs - lower * dprev) * r;
-            cp[i] = cprev;
-            dv[i] = dprev;
-            lprev = lri;
-            xm = x0;
-            x0 = x1;
-            x1 = (i + 2 <= N) ? x[i + 2] : x1;
+        const double* __restrict__ x = p.knots + k0;
+        const double2* __restrict__ lr = p.lr + (k0 - f);
+        double* __restrict__ sc = p.cr + 4 * k0;  // per row: c', then y, v, w
+        const int P = min(32, max(1, n / 2));
+        double y0 = 0.0, v0 = 0.0, w0 = 0.0, yL = 0.0, vL = 0.0, wL = 0.0;
+        const int r0 = (int)((int64_t)lane * n / P), r1 = (int)((int64_t)(lane + 1) * n / P);
+        if (lane < P) {
+            // forward elimination of the block, three right-hand sides
+            double cprev = 0.0, yprev = 0.0, vprev = 0.0, wlast = 0.0;
+#pragma unroll 4
+            for (int i = r0; i < r1; ++i) {
+                const double hl = i > 0 ? x[i] - x[i - 1] : 0.0;
+                const double hr = i < N ? x[i + 1] - x[i] : 0.0;
+                const double rhs = (i > 0 ? lr[i - 1].y : 0.0) + (i < N ? lr[i].x : 0.0);
+                const double lower = i > r0 ? hl * kSixth : 0.0;  // coupling inside the block
+                const double upper = hr * kSixth;
+                const double r = 1.0 / ((hl + hr) * kThird - lower * cprev);
+                const double yv = (rhs - lower * yprev) * r;
+                const double vv = ((i == r0 ? hl * kSixth : 0.0) - lower * vprev) * r;
+                cprev = i + 1 < r1 ? upper * r : 0.0;
+                if (i + 1 == r1) wlast = upper * r;  // w'_{m-1}: the coupling to the next block
+                sc[4 * i] = cprev;
+                sc[4 * i + 1] = yv;
+                sc[4 * i + 2] = vv;
+                yprev = yv;
+                vprev = vv;
+            }
+            // back substitution: y_j, v_j, w_j (w' is zero above the last row)
+            double yn = 0.0, vn = 0.0, wn = 0.0;
+#pragma unroll 4
+            for (int i = r1 - 1; i >= r0; --i) {
+                const double c = sc[4 * i];
+                const double yv = sc[4 * i + 1] - c * yn;
+                const double vv = sc[4 * i + 2] - c * vn;
+                const double wv = (i == r1 - 1 ? wlast : 0.0) - c * wn;
+                sc[4 * i + 1] = yv;
+                sc[4 * i + 2] = vv;
+                sc[4 * i + 3] = wv;
+                yn = yv;
+                vn = vv;
+                wn = wv;
+                if (i == r1 - 1) {
+                    yL = yv;
+                    vL = vv;
+                    wL = wv;
+                }
+            }
+            y0 = yn;
+            v0 = vn;
+            w0 = wn;
         }
-        double v = dv[N];
-        for (int i = N - 1; i >= 0; --i) {
-            v = dv[i] - cp[i] * v;
-            dv[i] = v;
+        // boundary unknowns, forward over the blocks in lane order.  Every lane
+        // runs the same recurrence on shuffled (uniform) inputs; lane q keeps
+        // block q's coefficients.  Carried: L_{q-1} = alpha + beta F_q.
+        double alpha = 0.0, beta = 0.0;
+        double gq_own = 0.0, dq_own = 0.0, aq_own = 0.0, bq_own = 0.0;
+        for (int q = 0; q < P; ++q) {
+            const double y0q = __shfl_sync(0xffffffffu, y0, q), v0q = __shfl_sync(0xffffffffu, v0, q);
+            const double w0q = __shfl_sync(0xffffffffu, w0, q), yLq = __shfl_sync(0xffffffffu, yL, q);
+            const double vLq = __shfl_sync(0xffffffffu, vL, q), wLq = __shfl_sync(0xffffffffu, wL, q);
+            // F_q = y0 - v0 L_{q-1} - w0 F_{q+1}  ->  F_q = g + d F_{q+1}
+            const double piv = 1.0 / (1.0 + v0q * beta);
+            const double g = (y0q - v0q * alpha) * piv;
+            const double d = -w0q * piv;
+            // L_q = yL - vL L_{q-1} - wL F_{q+1}  ->  L_q = an + bn F_{q+1}
+            const double an = yLq - vLq * (alpha + beta * g);
+            const double bn = -(vLq * beta * d + wLq);
+            if (lane == q) {
+                gq_own = g;
+                dq_own = d;
+                aq_own = an;
+                bq_own = bn;
+            }
+            alpha = an;
+            beta = bn;
+        }
+        // backward from F_P = 0: F_q = g_q + d_q F_{q+1}, L_q = a_q + b_q F_{q+1}
+        double Fnext = 0.0, Fq = 0.0, Lq = 0.0;
+        for (int q = P - 1; q >= 0; --q) {
+            const double gq = __shfl_sync(0xffffffffu, gq_own, q), dq = __shfl_sync(0xffffffffu, dq_own, q);
+            const double aq = __shfl_sync(0xffffffffu, aq_own, q), bq = __shfl_sync(0xffffffffu, bq_own, q);
+            if (lane == q) {
+                Fq = Fnext;  // F_{q+1}, the unknown after this lane's block
+                Lq = aq + bq * Fnext;
+            }
+            Fnext = gq + dq * Fnext;
+        }
+        // L_{p-1} from the previous lane (0 before the first block)
+        double Lprev = __shfl_up_sync(0xffffffffu, Lq, 1);
+        if (lane == 0) Lprev = 0.0;
+        if (lane < P) {
+            double* __restrict__ v = p.values + k0;
+#pragma unroll 4
+            for (int i = r0; i < r1; ++i) v[i] = sc[4 * i + 1] - sc[4 * i + 2] * Lprev - sc[4 * i + 3] * Fq;
         }
     }
 }
@@ -270,6 +364,10 @@ const GaussLegendre& gauss_legendre_rule(int Q)
                 rules[q].wl[i] = rules[q].w[i] * (1.0 - rules[q].x[i]) * 0.5;
                 rules[q].wr[i] = rules[q].w[i] * (1.0 + rules[q].x[i]) * 0.5;
                 rules[q].xf[i] = (float)rules[q].x[i];
+                rules[q].wlh[i] = (float)rules[q].wl[i];
+                rules[q].wll[i] = (float)(rules[q].wl[i] - (double)rules[q].wlh[i]);
+                rules[q].wrh[i] = (float)rules[q].wr[i];
+                rules[q].wrl[i] = (float)(rules[q].wr[i] - (double)rules[q].wrh[i]);
             }
         }
     });
@@ -309,9 +407,11 @@ pwl_status project_launch(const ProjectPlan& p, const GaussLegendre& gl, cudaStr
         hat_integrals_kernel<double><<<grid, 128, 0, s>>>(p, gl);
     PWL_CHECK_LAUNCH("hat_integrals_kernel");
     if (p.solver == 1) {
-        const int grid_t = (int)std::min<int64_t>((p.F + 63) / 64, (int64_t)di.sms * 16);
-        gram_thomas_kernel<<<grid_t, 64, 0, s>>>(p);
-        PWL_CHECK_LAUNCH("gram_thomas_kernel");
+        // two warps (functions) per CTA, so that a few hundred functions
+        // still spread over every SM
+        const int grid_w = (int)std::min<int64_t>((p.F + 1) / 2, (int64_t)di.sms * 32);
+        gram_spike_kernel<<<grid_w, 64, 0, s>>>(p, p.order);
+        PWL_CHECK_LAUNCH("gram_spike_kernel");
         return PWL_OK;
     }
     const size_t smem = sizeof(double) * 4 * (size_t)p.max_rows;

@@ -65,9 +65,11 @@ def _check_batch_eval(b, funcs, qo, x, y):
         assert np.abs(got[ok] - ref[ok]).max() <= EVAL_REL * np.abs(vv).max(), f
 
 
-@pytest.mark.parametrize("form", ["interp", "project"])
-def test_batch_design_values_eval_match_oracle(pwl, workloads, form):
-    funcs, n_int, qo, x = _batch_inputs(workloads, 40, seed=11)
+@pytest.mark.parametrize("form,F", [("interp", 40), ("project", 40), ("project", 70)])
+def test_batch_design_values_eval_match_oracle(pwl, workloads, form, F):
+    # F = 40: one CTA per function solves the Gram system (cyclic reduction);
+    # F = 70: one warp per function (partitioned Thomas)
+    funcs, n_int, qo, x = _batch_inputs(workloads, F, seed=11)
     mper = 16
     b = pwl.Batch(funcs, n_int, m_per_interval=mper)
     b.design()
@@ -106,7 +108,7 @@ def test_batch_staged_and_direct_pieces_agree(pwl, workloads, cells_per_knot):
     b.build()
     xd = torch.tensor(x, device="cuda")
     outs = []
-    for shape in range(4):
+    for shape in range(5):
         for stage_min in (0, 16, 1 << 30):
             b.plan(qo, shape, stage_min)
             info = b.info()
@@ -125,7 +127,7 @@ def test_batch_staged_and_direct_pieces_agree(pwl, workloads, cells_per_knot):
 @pytest.mark.parametrize("stage_min", [1, 16, 1 << 30])
 def test_batch_many_functions_per_cta(pwl, workloads, stage_min):
     # 600 functions for ~150 CTAs: every CTA walks several functions, so the
-    # asynchronous path (shape 0) alternates its two record buffers and
+    # asynchronous path (shape 4) alternates its two record buffers and
     # prefetches across staged and unstaged pieces
     funcs, n_int, qo, x = _batch_inputs(workloads, 600, seed=17, knots_hi=300, q_hi=2e4)
     b = pwl.Batch(funcs, n_int, m_per_interval=4)
@@ -133,7 +135,7 @@ def test_batch_many_functions_per_cta(pwl, workloads, stage_min):
     b.project("project")
     b.build()
     xd = torch.tensor(x, device="cuda")
-    b.plan(qo, 0, stage_min)
+    b.plan(qo, 4, stage_min)  # the asynchronous (bulk copy) shape
     info = b.info()
     assert info["n_items"] > info["eval_grid"]
     y = b.eval(xd).cpu().numpy()
@@ -179,7 +181,7 @@ def test_batch_autotune_keeps_results(pwl, workloads):
     y = torch.empty_like(xd)
     b.autotune(xd, y, reps=1)
     info = b.info()
-    assert 0 <= info["eval_shape"] < 4 and info["stage_min"] in (0, 4, 16, 64)
+    assert 0 <= info["eval_shape"] < 5 and info["stage_min"] in (0, 4, 16, 64)
     b.check()  # no staging wait timed out
     got = b.eval(xd).cpu().numpy()
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
