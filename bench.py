@@ -358,6 +358,8 @@ def run_ours(args):
     # fwd + bwd on the same tables and query sets
     fb = fwd_bwd(wl, args.fwd_bwd_steps)
     errors = wl.error_report()
+    ceiling = compute_ceiling(wl)
+    small = small_case(wl)
     e2e = None if args.no_e2e else run_e2e(wl, args.e2e_steps)
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -400,6 +402,8 @@ def run_ours(args):
         "design_ms_per_step": round(design_ms, 3),
         "fwd_bwd": fb,
         "errors_N4096": errors,
+        "compute_ceiling": ceiling,
+        "small_case": small,
         "gpu_launches": gpu_launches_per_step(wl) * args.steps,
         "clocks": clk,
     }
@@ -410,6 +414,44 @@ def run_ours(args):
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
     dist.close()
+
+
+def compute_ceiling(wl, m: int = 1 << 28, reps: int = 5):
+    """Algorithm 1 on 2^28 queries generated in registers (no query loads,
+    no result stores): the compute ceiling in ps per evaluation, on the
+    Gaussian N = 256 P_T table and the N = 4096 one."""
+    torch, pwl = wl.torch, wl.pwl
+    out = {}
+    acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for fi, N, kn, vi, vp, wsd, wsp, ti, tp in wl.items:
+        if fi != 0 or N not in (256, 4096):
+            continue
+        sec = time_launches(lambda: pwl.pwl_eval_synthetic(tp.handle, m, 7, acc), reps)
+        out[f"gaussian/project/N{N}"] = {"ps_per_eval": round(sec / m * 1e12, 3),
+                                         "G_evals_per_s": round(m / sec / 1e9, 1)}
+    return out
+
+
+def small_case(wl, reps: int = 50):
+    """The small configuration: exp(-x^2/2) on [-4, 4] with 63 intervals (64
+    knots), 10^6 uniform FP32 queries (seed 0), both forms: time per
+    evaluation launch and the max error against FP64 f."""
+    torch, pwl, W = wl.torch, wl.pwl, wl.W
+    sc = W.SMALL
+    f = sc["func"]
+    x = W.uniform_queries(f, sc["m"], seed=sc["seed"])
+    y = torch.empty_like(x)
+    kn = pwl.pwl_design(f, sc["n_intervals"])
+    out = {"n_intervals": sc["n_intervals"], "queries": sc["m"]}
+    xd = x.cpu().numpy().astype(np.float64)
+    for form in FORMS:
+        t = pwl.Table(kn, pwl.pwl_project(f, kn, form))
+        sec = time_launches(lambda: pwl.pwl_eval(t.handle, x, y), reps)
+        err = float(np.abs(y.cpu().numpy().astype(np.float64) - f64("gaussian", xd)).max())
+        out[form] = {"us_per_launch": round(sec * 1e6, 2), "G_evals_per_s": round(sc["m"] / sec / 1e9, 1),
+                     "max_err_vs_f64_f": err}
+        t.close()
+    return out
 
 
 def gpu_launches_per_step(wl) -> int:
@@ -458,26 +500,49 @@ def fwd_bwd(wl, steps):
 
 def run_e2e(wl, steps):
     """Same metric through the public API with host buffers: every step copies
-    its query sets from pinned host memory and reads every result back."""
+    its query sets from pinned host memory and reads every result back.  The
+    copies run on their own streams (host-to-device on one, device-to-host on
+    another) and overlap the design graph and the evaluations; two result
+    buffers alternate, each reused only after its previous read-back."""
     torch, pwl = wl.torch, wl.pwl
     hx = {k: v.cpu().pin_memory() for k, v in wl.x.items()}
     hy = torch.empty(wl.m, dtype=torch.float32).pin_memory()
-    dx = {fi: torch.empty(wl.m, dtype=torch.float32, device="cuda") for fi in range(len(wl.funcs))}
-    dx2 = {fi: torch.empty(wl.m, dtype=torch.float32, device="cuda") for fi in range(len(wl.funcs))}
+    dx = {k: torch.empty(wl.m, dtype=torch.float32, device="cuda") for k in wl.x}
+    ys = [torch.empty(wl.m, dtype=torch.float32, device="cuda") for _ in range(2)]
+    comp = torch.cuda.current_stream()
+    h2d_s, d2h_s = torch.cuda.Stream(), torch.cuda.Stream()
+    uploaded = {k: torch.cuda.Event() for k in wl.x}
+    read = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in read:
+        e.record(d2h_s)
 
     def one():
         h2d = d2h = 0
+        # inputs of this step, overlapping the design graph
+        h2d_s.wait_stream(comp)  # the previous step's evaluations are done with dx
+        with torch.cuda.stream(h2d_s):
+            for k in wl.x:
+                dx[k].copy_(hx[k], non_blocking=True)
+                uploaded[k].record(h2d_s)
+                h2d += wl.m * 4
         wl.design_and_tables()
-        for fi in range(len(wl.funcs)):
-            dx[fi].copy_(hx[(fi, "uniform")], non_blocking=True)
-            dx2[fi].copy_(hx[(fi, "normal")], non_blocking=True)
-            h2d += 2 * wl.m * 4
+        j = 0
         for fi, N, kn, vi, vp, wsd, wsp, ti, tp in wl.items:
             for t in (ti, tp):
-                for xs in (dx[fi], dx2[fi]):
-                    pwl.pwl_eval(t.handle, xs, wl.y)
-                    hy.copy_(wl.y, non_blocking=True)
+                for qs in ("uniform", "normal"):
+                    b = j & 1
+                    comp.wait_event(uploaded[(fi, qs)])
+                    comp.wait_event(read[b])  # the buffer's previous result has been read
+                    pwl.pwl_eval(t.handle, dx[(fi, qs)], ys[b])
+                    done[b].record(comp)
+                    d2h_s.wait_event(done[b])
+                    with torch.cuda.stream(d2h_s):
+                        hy.copy_(ys[b], non_blocking=True)
+                        read[b].record(d2h_s)
                     d2h += wl.m * 4
+                    j += 1
+        comp.wait_stream(d2h_s)  # the step ends when its last result is on the host
         return h2d, d2h
 
     one()
@@ -491,7 +556,8 @@ def run_e2e(wl, steps):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     return {"value": round(wl.evals_per_step * steps / (ms / 1e3) / 1e9, 3), "unit": "G evals/s",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "overlap": "H2D and D2H on their own streams, two result buffers"}
 
 
 # ----------------------------------------------------------------------------

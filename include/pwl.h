@@ -216,6 +216,18 @@ pwl_status pwl_eval(pwl_table t, const void* d_x, void* d_y, int64_t m, int32_t 
 pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* d_y, int64_t m,
                             void* stream);
 
+/* Compute ceiling of Algorithm 1 (the analogue of the paper's synthetic
+ * timings, Table I): the table is evaluated at m queries generated in
+ * registers, with no query read from memory and no result written.  Query q
+ * (0 <= q < m <= 2^32) is x_q = u_q (b - a) + a in FP32 (a product and a
+ * sum, each rounded to nearest), where a, b are the table's FP32 end knots
+ * and u_q = (lowbias32((q + seed) mod 2^32) >> 8) / 2^24, lowbias32 being
+ * the 32-bit integer hash of the hash-prospector project (x ^= x >> 16;
+ * x *= 0x7feb352d; x ^= x >> 15; x *= 0x846ca68b; x ^= x >> 16).  Every CTA
+ * adds the FP32 sum of its results (in an unspecified order) to *d_sum, a
+ * device FP64 word the caller zeroes: a checksum that keeps the work live.  */
+pwl_status pwl_eval_synthetic(pwl_table t, uint32_t seed, int64_t m, double* d_sum, void* stream);
+
 /* Backward of pwl_eval for upstream gradients gy (FP32, m elements):
  *   gx[q] = gy[q] * s_i (s_i the slope of x[q]'s interval; 0 if clamped)
  *   g_values[j] += sum over queries of gy * dy/dv_j  (N+1 FP32, or NULL)

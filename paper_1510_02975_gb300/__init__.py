@@ -18,7 +18,7 @@ from ._capi import (DTYPES, FORMS, KINDS, PRECISIONS, PwlBatchInfo, PwlError, Pw
 
 __all__ = [
     "PwlError", "pwl_design", "pwl_project", "pwl_table_build", "pwl_table_update", "pwl_table_check", "pwl_table_destroy", "pwl_table_get_info",
-    "pwl_eval", "pwl_eval_variant", "pwl_eval_backward", "pwl_eval_backward_noalloc",
+    "pwl_eval", "pwl_eval_variant", "pwl_eval_synthetic", "pwl_eval_backward", "pwl_eval_backward_noalloc",
     "pwl_batch_create", "pwl_batch_destroy", "pwl_batch_design", "pwl_batch_project", "pwl_batch_build",
     "pwl_batch_check", "pwl_batch_plan", "pwl_batch_eval", "pwl_batch_autotune", "pwl_batch_get_info", "Batch",
     "pwl_channels_forward", "pwl_channels_backward", "ChannelPWL", "Table", "design", "project", "PWLFunction",
@@ -161,6 +161,18 @@ def pwl_eval_variant(handle, mode: int, x, y=None, stream=None):
     check(load().pwl_eval_variant(ctypes.c_void_p(handle), mode, _ptr(x), _ptr(y), x.numel(), _stream(stream)),
           "pwl_eval_variant")
     return y
+
+
+def pwl_eval_synthetic(handle, m: int, seed: int = 0, out=None, stream=None):
+    """Compute-ceiling run: Algorithm 1 on m queries generated in registers;
+    returns (or adds into `out`) the float64 checksum of the results."""
+    torch = _torch()
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _require(out, torch.float64, "out", 1)
+    check(load().pwl_eval_synthetic(ctypes.c_void_p(handle), int(seed) & 0xFFFFFFFF, int(m), _ptr(out),
+                                    _stream(stream)), "pwl_eval_synthetic")
+    return out
 
 
 def pwl_eval_backward(handle, x, gy, gx=None, g_values=None, g_knots=None, workspace=None, stream=None):

@@ -70,6 +70,7 @@ SIGNATURES = {
     "pwl_table_get_info": (_ST, [_P, ctypes.POINTER(PwlTableInfo)]),
     "pwl_eval": (_ST, [_P, _P, _P, _I64, _I32, _P]),
     "pwl_eval_variant": (_ST, [_P, _I32, _P, _P, _I64, _P]),
+    "pwl_eval_synthetic": (_ST, [_P, ctypes.c_uint32, _I64, _P, _P]),
     "pwl_eval_backward_workspace_size": (_SZ, [_P]),
     "pwl_eval_backward": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P, _SZ, _P]),
     "pwl_eval_backward_noalloc": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P]),

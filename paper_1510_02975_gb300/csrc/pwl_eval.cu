@@ -232,6 +232,78 @@ __global__ void __launch_bounds__(1024, MINB) eval_kernel(const EvalArgs args, c
     }
 }
 
+// ---- compute ceiling: queries generated in registers -----------------------
+// The query stream of pwl_eval_synthetic: u_q = top 24 bits of lowbias32(q +
+// seed) / 2^24 (the 32-bit integer hash "lowbias32" of the hash-prospector
+// project: xor-shift 16, multiply 0x7feb352d, xor-shift 15, multiply
+// 0x846ca68b, xor-shift 16), x_q = u_q (b - a) + a in FP32 (two roundings).
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+template <class L>
+__device__ __forceinline__ float synth_sum(const L& f, uint32_t seed, float a, float w, int64_t m)
+{
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    float acc = 0.0f;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += nthr) {
+        const float u = (float)(lowbias32((uint32_t)q + seed) >> 8) * 0x1p-24f;
+        acc += f(__fadd_rn(__fmul_rn(u, w), a));
+    }
+    return acc;
+}
+
+// Algorithm 1 on m generated queries: no query loaded, no result stored;
+// every CTA adds the sum of its results to *sum (FP64).  The staging and the
+// lookup are those of eval_kernel.
+template <int LAYOUT, int MINB>
+__global__ void __launch_bounds__(1024, MINB) eval_synth_kernel(const EvalArgs args, uint32_t seed, int64_t m,
+                                                                double* sum)
+{
+    extern __shared__ float4 s_fwd[];
+    EvalArgs p = args;
+    const float w = __fsub_rn(p.b, p.a);
+    float acc;
+    if (LAYOUT == 0) {
+        float2* sP = reinterpret_cast<float2*>(s_fwd);
+        float2* sS = sP + p.K;
+        const int n_chain = p.hdr->n_chain_f;
+        p.max_chain = p.hdr->max_chain_f;
+        for (int i = threadIdx.x; i < p.K; i += blockDim.x) sP[i] = __ldg(p.recP + i);
+        if (p.s_staged)
+            for (int i = threadIdx.x; i < 2 * (p.N + 1); i += blockDim.x) sS[i] = __ldg(p.recS + i);
+        __syncthreads();
+        acc = n_chain == 0 ? synth_sum(Lerp8<false>{sP, sS, p}, seed, p.a, w, m)
+                           : synth_sum(Lerp8<true>{sP, sS, p}, seed, p.a, w, m);
+    } else {
+        const int n_chain = p.hdr->n_chain_b;
+        p.max_chain = p.hdr->max_chain_b;
+        p.n_smem = min(p.K + n_chain, p.n_smem);
+        for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) s_fwd[i] = __ldg(p.rec16 + i);
+        __syncthreads();
+        acc = n_chain == 0 ? synth_sum(Lerp16<false>{s_fwd, p}, seed, p.a, w, m)
+                           : synth_sum(Lerp16<true>{s_fwd, p}, seed, p.a, w, m);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    // the index may fill all of the shared memory: once every lookup is
+    // done, its first 32 words hold the warp sums
+    float* s_red = reinterpret_cast<float*>(s_fwd);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += (double)s_red[k];
+        atomicAdd(sum, t);
+    }
+}
+
 // ---- mode 0: Algorithm 1 with a binary search over the knots --------------
 __global__ void __launch_bounds__(1024) eval_search_kernel(const float* __restrict__ xk_g,
                                                            const float* __restrict__ vk_g, int N,
@@ -370,6 +442,49 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
     return PWL_OK;
 }
 
+pwl_status launch_synth(pwl_table t, uint32_t seed, int64_t m, double* sum, cudaStream_t s)
+{
+    EvalArgs p{};
+    p.recP = t->recP;
+    p.recS = t->recS;
+    p.xk = t->xk;
+    p.rec16 = t->rec16;
+    p.hdr = t->hdr;
+    p.N = (int)t->N;
+    p.a = t->a;
+    p.b = t->b;
+    size_t smem;
+    if (t->layout == 0) {
+        p.K = (int)t->K;
+        p.s_staged = forward_side_staged(t->N) ? 1 : 0;
+        p.inv_w = t->inv_w;
+        p.off = t->off;
+        p.w = t->w;
+        smem = eval8_smem_bytes(t);
+    } else {
+        p.K = (int)t->Kb;
+        p.n_smem = (int)eval16_smem_records(t);
+        p.inv_w = t->inv_w_b;
+        p.off = t->off_b;
+        smem = eval16_smem_bytes(t);
+        if (p.n_smem < p.K) return fail(PWL_ENOTSUP, "16-byte index of %d cells does not fit one CTA", p.K);
+    }
+    const DeviceInfo& di = device_info();
+    if (smem > di.smem_optin) return fail(PWL_ENOTSUP, "forward index of %zu bytes does not fit one CTA", smem);
+    const bool two = di.smem_per_sm >= 2 * (smem + 1024);
+    void (*kern)(const EvalArgs, uint32_t, int64_t, double*);
+    if (t->layout == 0)
+        kern = two ? eval_synth_kernel<0, 2> : eval_synth_kernel<0, 1>;
+    else
+        kern = two ? eval_synth_kernel<1, 2> : eval_synth_kernel<1, 1>;
+    int max_grid = 0;
+    PWL_CUDA_TRY(occupancy_grid(kern, 1024, smem, &max_grid));
+    const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, (m + 4095) / 4096));
+    kern<<<grid, 1024, smem, s>>>(p, seed, m, sum);
+    PWL_CHECK_LAUNCH("eval_synth_kernel");
+    return PWL_OK;
+}
+
 pwl_status ensure_texture(pwl_table t)
 {
     if (t->tex) return PWL_OK;
@@ -421,6 +536,19 @@ pwl_status pwl_eval(pwl_table t, const void* d_x, void* d_y, int64_t m, int32_t 
         return launch_eval<__half>(t, t->layout, static_cast<const __half*>(d_x), static_cast<__half*>(d_y), m, s);
     }
     return fail(PWL_EINVAL, "unknown io dtype %d", io_dtype);
+}
+
+pwl_status pwl_eval_synthetic(pwl_table t, uint32_t seed, int64_t m, double* d_sum, void* stream)
+{
+    clear_error();
+    if (!t) return fail(PWL_EINVAL, "table is NULL");
+    if (m < 0 || m > ((int64_t)1 << 32)) return fail(PWL_EINVAL, "m must be in [0, 2^32]");
+    if (!d_sum) return fail(PWL_EINVAL, "d_sum is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
+    if (m == 0) return PWL_OK;
+    return launch_synth(t, seed, m, d_sum, as_stream(stream));
 }
 
 pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* d_y, int64_t m,

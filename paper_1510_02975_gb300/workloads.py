@@ -43,6 +43,30 @@ def uniform_queries(desc, m: int, seed: int, device="cuda", dtype=None):
     return x if dtype is None else x.to(dtype)
 
 
+def lowbias32(v):
+    """The 32-bit integer hash "lowbias32" (hash-prospector project), on a
+    numpy uint32 array: xor-shift 16, multiply 0x7feb352d, xor-shift 15,
+    multiply 0x846ca68b, xor-shift 16 (all mod 2^32)."""
+    v = np.asarray(v, dtype=np.uint32).copy()
+    v ^= v >> np.uint32(16)
+    v *= np.uint32(0x7FEB352D)
+    v ^= v >> np.uint32(15)
+    v *= np.uint32(0x846CA68B)
+    v ^= v >> np.uint32(16)
+    return v
+
+
+def synthetic_queries(a: float, b: float, m: int, seed: int = 0) -> np.ndarray:
+    """The generated query stream of pwl_eval_synthetic, as float32: x_q =
+    u_q (b - a) + a with u_q = (lowbias32(q + seed) >> 8) / 2^24, a and b
+    the table's float32 end knots, each operation rounded to float32."""
+    q = (np.arange(m, dtype=np.uint64) + np.uint64(seed)) & np.uint64(0xFFFFFFFF)
+    u = (lowbias32(q.astype(np.uint32)) >> np.uint32(8)).astype(np.float32) * np.float32(2.0 ** -24)
+    a32, b32 = np.float32(a), np.float32(b)
+    w = np.float32(b32 - a32)
+    return (u * w + a32).astype(np.float32)
+
+
 def normal_queries(desc, m: int, seed: int, sigma: float = 1.5, device="cuda", dtype=None):
     """m float32 queries normal(0, sigma) clipped to [a, b]."""
     import torch

@@ -339,3 +339,21 @@ def test_design_projection_update_eval_in_a_cuda_graph(pwl, workloads):
     assert torch.equal(knots, k_eager)
     assert torch.equal(y, y_eager)
     t.close()
+
+
+@pytest.mark.parametrize("N,k_cells", [(256, 0), (4096, 0), (300, 40)])
+def test_eval_synthetic_checksum_matches_oracle(pwl, workloads, N, k_cells):
+    # compute-ceiling mode: the generated queries are rebuilt on the host from
+    # the same hash; the GPU checksum of Algorithm 1 over them equals the
+    # oracle's sum within the FP32 evaluation bound plus FP32 summation
+    # (every thread sums its share in FP32)
+    f = workloads.PAPER_FUNCTIONS["lorentzian"]
+    t, xk, vk = _table_and_ref(pwl, f, N, "project", "fp32", k_cells)
+    m, seed = (1 << 20) + 7, 12345
+    got = pwl.pwl_eval_synthetic(t.handle, m, seed).item()
+    x = workloads.synthetic_queries(float(t.info["a"]), float(t.info["b"]), m, seed).astype(np.float64)
+    ref_y = oracle.evaluate(xk, vk, x)
+    ref = float(np.sum(ref_y))
+    bound = m * EVAL_REL * np.abs(vk).max() + 1e-5 * float(np.sum(np.abs(ref_y)))
+    assert abs(got - ref) <= bound
+    t.close()
