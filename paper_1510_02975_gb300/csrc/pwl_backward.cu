@@ -40,6 +40,7 @@ struct BwdArgs {
     const float* inv_h;
     const float* slope;
     int N, K, n_smem, max_chain;
+    int lanes;          // accumulator copies (1, 8 or 32), lane l adds into copy l mod lanes
     float a, b, inv_w, off;
     float s_first, s_last;  // slopes of intervals 1 and N (set by the kernel)
     int64_t nvec;       // float4 vectors (x, gy and gx all 16-byte aligned), else 0
@@ -53,58 +54,49 @@ struct EndSums {
     float clamped_left, clamped_right, at_a, at_b;
 };
 
+// One query, without branches apart from chain walks: the lookup runs on the
+// clamped point (a NaN looks up a and contributes nothing), the interval and
+// the side come from selects, and one predicated pair of shared-memory
+// atomics takes an interior query's two sums (a divergent version issued the
+// atomics once per path: 4x the atomic instructions).
 template <bool CHAINS>
 __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restrict__ srec,
                                          const float* __restrict__ s_ih, float* accA, float* accB,
-                                         EndSums& e, const BwdArgs& p)
+                                         EndSums& e, const BwdArgs& p, int copy)
 {
-    if (x != x) return x;  // NaN: no table contribution
-    if (x <= p.a) {
-        if (x < p.a) {
-            e.clamped_left += g;
-            return 0.0f;
-        }
-        e.at_a += g;  // interval 1, delta = 0
-        return g * p.s_first;
-    }
-    if (x >= p.b) {
-        if (x > p.b) {
-            e.clamped_right += g;
-            return 0.0f;
-        }
-        e.at_b += g;  // interval N, delta = 1
-        return g * p.s_last;
-    }
-    const int c = cell_of(x, p.inv_w, p.off, p.K);
+    const float xc = fminf(fmaxf(x, p.a), p.b);  // NaN -> a
+    const int c = cell_of(xc, p.inv_w, p.off, p.K);
     float4 r = (c < p.n_smem) ? srec[c] : __ldg(p.rec + c);
     if (CHAINS) {
-        for (int it = 0; it < p.max_chain && x >= r.x && is_link(r.w); ++it) {
+        for (int it = 0; it < p.max_chain && xc >= r.x && is_link(r.w); ++it) {
             const int j = link_index(r.w);
             r = (j < p.n_smem) ? srec[j] : __ldg(p.rec + j);
         }
     }
     const int j = __float_as_int(r.y);
-    int i;
-    float s, one_minus, delta;
-    if (x < r.x) {  // interval j, measured from its right end
-        i = j;
-        s = r.z;
-        one_minus = (r.x - x) * s_ih[j];
-        delta = 1.0f - one_minus;
-    } else if (j < p.N) {  // interval j + 1
-        i = j + 1;
-        s = r.w;
-        delta = (x - r.x) * s_ih[j + 1];
-        one_minus = 1.0f - delta;
-    } else {  // x == x_N: interval N with delta = 1
-        i = p.N;
-        s = r.z;
-        delta = 1.0f;
-        one_minus = 0.0f;
+    // left of x_j: interval j, measured from its right end; else interval
+    // j + 1 (an interior query never reaches x_N, where j + 1 would be N + 1)
+    const bool lside = xc < r.x;
+    const int i = lside ? j : j + 1;
+    const float s = lside ? r.z : r.w;
+    const float tt = (lside ? (r.x - xc) : (xc - r.x)) * s_ih[i];
+    const float delta = lside ? 1.0f - tt : tt;
+    const float one_minus = lside ? tt : 1.0f - tt;
+    const bool interior = x > p.a && x < p.b;  // false for NaN
+    if (interior) {
+        atomicAdd(accA + i * p.lanes + copy, g * one_minus);
+        atomicAdd(accB + i * p.lanes + copy, g * delta);
     }
-    atomicAdd(accA + i, g * one_minus);
-    atomicAdd(accB + i, g * delta);
-    return g * s;
+    // the ends: clamped queries feed g_v[0] or g_v[N]; x = a is interval 1 at
+    // delta = 0, x = b interval N at delta = 1
+    e.clamped_left += x < p.a ? g : 0.0f;
+    e.at_a += x == p.a ? g : 0.0f;
+    e.clamped_right += x > p.b ? g : 0.0f;
+    e.at_b += x == p.b ? g : 0.0f;
+    float gx = interior ? g * s : 0.0f;
+    gx = x == p.a ? g * p.s_first : gx;
+    gx = x == p.b ? g * p.s_last : gx;
+    return x != x ? x : gx;
 }
 
 template <bool CHAINS>
@@ -114,6 +106,7 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
 {
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int copy = threadIdx.x & (p.lanes - 1);
     const float4* xv = reinterpret_cast<const float4*>(x);
     const float4* gv = reinterpret_cast<const float4*>(gy);
     float4* ov = reinterpret_cast<float4*>(gx);
@@ -128,24 +121,24 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
 #pragma unroll
         for (int u = 0; u < kBwdUnroll; ++u) {
             float4 o;
-            o.x = bwd_one<CHAINS>(xs[u].x, gs[u].x, srec, s_ih, accA, accB, e, p);
-            o.y = bwd_one<CHAINS>(xs[u].y, gs[u].y, srec, s_ih, accA, accB, e, p);
-            o.z = bwd_one<CHAINS>(xs[u].z, gs[u].z, srec, s_ih, accA, accB, e, p);
-            o.w = bwd_one<CHAINS>(xs[u].w, gs[u].w, srec, s_ih, accA, accB, e, p);
+            o.x = bwd_one<CHAINS>(xs[u].x, gs[u].x, srec, s_ih, accA, accB, e, p, copy);
+            o.y = bwd_one<CHAINS>(xs[u].y, gs[u].y, srec, s_ih, accA, accB, e, p, copy);
+            o.z = bwd_one<CHAINS>(xs[u].z, gs[u].z, srec, s_ih, accA, accB, e, p, copy);
+            o.w = bwd_one<CHAINS>(xs[u].w, gs[u].w, srec, s_ih, accA, accB, e, p, copy);
             __stcs(ov + i + u * nthr, o);
         }
     }
     for (; i < p.nvec; i += nthr) {
         const float4 xs = __ldcs(xv + i), gs = __ldcs(gv + i);
         float4 o;
-        o.x = bwd_one<CHAINS>(xs.x, gs.x, srec, s_ih, accA, accB, e, p);
-        o.y = bwd_one<CHAINS>(xs.y, gs.y, srec, s_ih, accA, accB, e, p);
-        o.z = bwd_one<CHAINS>(xs.z, gs.z, srec, s_ih, accA, accB, e, p);
-        o.w = bwd_one<CHAINS>(xs.w, gs.w, srec, s_ih, accA, accB, e, p);
+        o.x = bwd_one<CHAINS>(xs.x, gs.x, srec, s_ih, accA, accB, e, p, copy);
+        o.y = bwd_one<CHAINS>(xs.y, gs.y, srec, s_ih, accA, accB, e, p, copy);
+        o.z = bwd_one<CHAINS>(xs.z, gs.z, srec, s_ih, accA, accB, e, p, copy);
+        o.w = bwd_one<CHAINS>(xs.w, gs.w, srec, s_ih, accA, accB, e, p, copy);
         __stcs(ov + i, o);
     }
     for (int64_t q = p.nvec * 4 + tid; q < m; q += nthr)
-        gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, e, p);
+        gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, e, p, copy);
 }
 
 __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, const float* x, const float* gy,
@@ -155,7 +148,7 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     float4* srec = s_dyn;
     float* s_ih = reinterpret_cast<float*>(s_dyn + args.n_smem);
     float* accA = s_ih + (args.N + 2);
-    float* accB = accA + (args.N + 2);
+    float* accB = accA + (size_t)(args.N + 2) * args.lanes;
     BwdArgs p = args;
     const int n_chain = p.hdr->n_chain_b;
     p.max_chain = p.hdr->max_chain_b;
@@ -163,11 +156,8 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     p.s_first = p.slope[1];
     p.s_last = p.slope[p.N];
     for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) srec[i] = __ldg(p.rec + i);
-    for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) {
-        s_ih[i] = p.inv_h[i];
-        accA[i] = 0.0f;
-        accB[i] = 0.0f;
-    }
+    for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) s_ih[i] = p.inv_h[i];
+    for (int i = threadIdx.x; i < 2 * (p.N + 2) * p.lanes; i += blockDim.x) accA[i] = 0.0f;
     __syncthreads();
     EndSums e{0.0f, 0.0f, 0.0f, 0.0f};
     if (n_chain == 0)
@@ -180,15 +170,22 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
         e.at_a += __shfl_xor_sync(0xffffffffu, e.at_a, o);
         e.at_b += __shfl_xor_sync(0xffffffffu, e.at_b, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if ((threadIdx.x & 31) == 0) {  // into copy 0
         atomicAdd(accA, e.clamped_left);
-        atomicAdd(accA + p.N + 1, e.clamped_right);
-        atomicAdd(accA + 1, e.at_a);
-        atomicAdd(accB + p.N, e.at_b);
+        atomicAdd(accA + (size_t)(p.N + 1) * p.lanes, e.clamped_right);
+        atomicAdd(accA + p.lanes, e.at_a);
+        atomicAdd(accB + (size_t)p.N * p.lanes, e.at_b);
     }
     __syncthreads();
+    // one warp per bin sums its copies (A bins, then B bins: bin k's copies
+    // are acc[k lanes .. k lanes + lanes - 1])
     float* row = partials + (size_t)blockIdx.x * 2 * (p.N + 2);
-    for (int k = threadIdx.x; k < 2 * (p.N + 2); k += blockDim.x) row[k] = accA[k];
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int k = threadIdx.x >> 5; k < 2 * (p.N + 2); k += nwarps) {
+        float v = lane < p.lanes ? accA[(size_t)k * p.lanes + lane] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) row[k] = v;
+    }
 }
 
 // g_v[j] += A_{j+1} + B_j (+ clamped terms), g_x[j] += -s_{j+1} A_{j+1} - s_j B_j
@@ -243,6 +240,7 @@ pwl_status backward_launch(pwl_table t, const float* x, const float* gy, float* 
     p.K = (int)t->Kb;
     p.n_smem = (int)sh.n_smem;
     p.max_chain = 0;
+    p.lanes = backward_lanes(t);
     p.a = t->a;
     p.b = t->b;
     p.inv_w = t->inv_w_b;
