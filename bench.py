@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--rows", type=int, default=65536, help="rows of x in --report channels")
     ap.add_argument("--batch-funcs", type=int, default=4096, help="functions in --report batched")
     ap.add_argument("--batch-m", type=int, default=16, help="density cells per interval in --report batched")
+    ap.add_argument("--batch-cpk", type=int, default=0,
+                    help="--report batched: index cells per knot (0: the library's default)")
     ap.add_argument("--no-per-function", action="store_true",
                     help="--report batched: skip the one-table-per-function comparison")
     return ap.parse_args()
@@ -776,7 +778,7 @@ def run_batched(args):
     x, qo = W.batch_queries(funcs, n_q, seed=6)
     y = torch.empty_like(x)
     nq = int(qo[-1])
-    b = pwl.Batch(funcs, n_int, m_per_interval=args.batch_m)
+    b = pwl.Batch(funcs, n_int, m_per_interval=args.batch_m, cells_per_knot=args.batch_cpk)
     prec = "fp32"
 
     def pipeline(stream=None):
@@ -811,7 +813,7 @@ def run_batched(args):
     ev_gbs = BYTES_FWD * nq / phases["eval"] / 1e9
     out = {
         "report": "batched", "n_funcs": len(funcs), "total_knots": int(info["total_knots"]),
-        "total_queries": nq, "m_per_interval": args.batch_m,
+        "total_queries": nq, "m_per_interval": args.batch_m, "cells_per_knot": args.batch_cpk or 4,
         "step_ms": round(step * 1e3, 4),
         "step_G_evals_per_s": round(nq / step / 1e9, 2),
         "phase_ms": {k: round(v * 1e3, 4) for k, v in phases.items()},

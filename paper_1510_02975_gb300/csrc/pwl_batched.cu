@@ -263,7 +263,9 @@ __device__ __forceinline__ void batch_range_ring(const Lookup& d, const float2* 
 
 struct EvalParams {
     const WorkItem* items;
-    const int* range;        // CTA b runs items range[b] .. range[b+1]-1
+    const int* range;        // range r holds items range[r] .. range[r+1]-1
+    int n_ranges;            // CTA b starts on range b, then takes gridDim + *counter++ (dynamic shapes)
+    int* counter;            // zeroed before every launch
     const BatchFunc* bf;
     const float* xk_all;
     const float2* recP;
@@ -323,10 +325,14 @@ template <int THREADS, int MINB, int U, int MODE, int D>
 __global__ void __launch_bounds__(THREADS, MINB) batch_eval_kernel(const EvalParams p, const float* x, float* y)
 {
     extern __shared__ __align__(16) float2 s_idx[];
+    __shared__ int s_next;
     float4* ring = reinterpret_cast<float4*>(s_idx + (MODE == 0 ? p.buf_stride : 0));
     int staged_f = -1;
-    const int it1 = p.range[blockIdx.x + 1];
-    for (int it = p.range[blockIdx.x]; it < it1; ++it) {
+    // the CTA's own range first, then unclaimed ones in order: the cost model
+    // balances the ranges, the counter absorbs what it misjudges
+    for (int rg = blockIdx.x; rg < p.n_ranges;) {
+    const int it1 = p.range[rg + 1];
+    for (int it = p.range[rg]; it < it1; ++it) {
         const WorkItem w = p.items[it];
         const BatchFunc& g = p.bf[w.f];
         if (MODE == 0 && w.staged) {
@@ -344,6 +350,11 @@ __global__ void __launch_bounds__(THREADS, MINB) batch_eval_kernel(const EvalPar
         } else {
             run_piece<U, D, false>(p, g, w, nullptr, x, y, ring);
         }
+    }
+    __syncthreads();  // every thread has read the previous s_next
+    if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(p.counter, 1);
+    __syncthreads();
+    rg = s_next;
     }
 }
 
@@ -438,6 +449,7 @@ __global__ void __launch_bounds__(1024, 1) batch_eval_async_kernel(const EvalPar
 using BatchEvalKernel = void (*)(const EvalParams, const float*, float*);
 enum StageKind { kStageAsync = 0, kStageSync = 1, kStageNone = 2 };
 constexpr int kRingDepth = 4;
+constexpr int kRangesPerCta = 3;  // cost-balanced ranges per CTA of a dynamic shape
 struct EvalShape {
     int threads;
     int ctas;   // CTAs per SM the shape is meant to run
@@ -495,6 +507,8 @@ struct pwl_batch_s {
     void* plan_dev;             // items, then the CTA ranges
     WorkItem* items;
     int* range;
+    int* counter;               // next dynamic range, zeroed before each launch
+    int n_ranges;
     int grid;
     int shape;
     int64_t stage_min;          // stage when queries * stage_min >= index bytes
@@ -837,16 +851,20 @@ pwl_status pwl_batch_plan(pwl_batch b, const int64_t* query_offsets, int32_t sha
     const size_t smem = (sh.stage == kStageAsync ? 2 * buf : (sh.stage == kStageSync ? buf : 0)) + ring;
     int grid = 0;
     PWL_CUDA_TRY(occupancy_grid(sh.kern, sh.threads, smem, &grid));
+    // ranges per CTA: several (taken dynamically after the first) except for
+    // the asynchronous shape, whose prefetch looks ahead inside one range
+    const int n_ranges = sh.stage == kStageAsync ? grid : grid * kRangesPerCta;
     std::vector<WorkItem> items;
     std::vector<int> range;
-    make_plan(b, query_offsets, grid, stage_min, budget, items, range);
+    make_plan(b, query_offsets, n_ranges, stage_min, budget, items, range);
     void* dev = nullptr;
     const size_t bytes_items = align256(sizeof(WorkItem) * std::max<size_t>(items.size(), 1));
-    PWL_CUDA_TRY(cudaMalloc(&dev, bytes_items + sizeof(int) * (size_t)(grid + 1)));
+    const size_t bytes_range = align256(sizeof(int) * (size_t)(n_ranges + 1));
+    PWL_CUDA_TRY(cudaMalloc(&dev, bytes_items + bytes_range + sizeof(int)));
     cudaError_t e = cudaSuccess;
     if (!items.empty()) e = cudaMemcpy(dev, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(static_cast<char*>(dev) + bytes_items, range.data(), sizeof(int) * (size_t)(grid + 1),
+        e = cudaMemcpy(static_cast<char*>(dev) + bytes_items, range.data(), sizeof(int) * (size_t)(n_ranges + 1),
                        cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dev);
@@ -856,6 +874,8 @@ pwl_status pwl_batch_plan(pwl_batch b, const int64_t* query_offsets, int32_t sha
     b->plan_dev = dev;
     b->items = static_cast<WorkItem*>(dev);
     b->range = reinterpret_cast<int*>(static_cast<char*>(dev) + bytes_items);
+    b->counter = reinterpret_cast<int*>(static_cast<char*>(dev) + bytes_items + bytes_range);
+    b->n_ranges = n_ranges;
     b->grid = grid;
     b->shape = shape;
     b->stage_min = stage_min;
@@ -881,7 +901,10 @@ pwl_status pwl_batch_eval(pwl_batch b, const float* d_x, float* d_y, void* strea
         return fail(PWL_EINVAL, "x and y must be 16-byte aligned");
     const EvalShape& sh = kShapes[b->shape];
     PWL_CUDA_TRY(cudaFuncSetAttribute(sh.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-    const EvalParams p{b->items, b->range, b->bf, b->xk, b->recP, b->recS, b->buf_stride, b->status};
+    const EvalParams p{b->items, b->range, b->n_ranges, b->counter, b->bf, b->xk, b->recP, b->recS,
+                       b->buf_stride, b->status};
+    if (sh.stage != kStageAsync)
+        PWL_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), as_stream(stream)));
     sh.kern<<<b->grid, sh.threads, b->smem, as_stream(stream)>>>(p, d_x, d_y);
     PWL_CHECK_LAUNCH("batch_eval_kernel");
     return PWL_OK;
