@@ -283,62 +283,51 @@ struct EndSums {
     float left, right;
 };
 
+// One element without branches apart from chain walks (a divergent version
+// issued the shared-memory atomics once per path): the lookup runs on the
+// clamped point (NaN looks up a and contributes nothing), the side and the
+// interval come from selects, and one predicated pair of atomics takes an
+// in-range element's two sums.  A knot-free cell's record {i, x_{i-1}} is
+// the right side of knot i - 1; a knot cell's {tag(k), x_k} either side of
+// knot k; so both read "knot k, point x_k".
 template <bool CHAINS>
 __device__ __forceinline__ float chan_bwd_one(float x, float g, int ch, const float* __restrict__ xs,
                                               const float2* sP, const float2* sI, const ChanConst& cc, int N,
                                               int K, float* accA, float* accB, EndSums& e)
 {
-    if (x != x) return x;  // NaN: no table contribution
-    if (x < cc.a) {
-        e.left += g;
-        return 0.0f;
-    }
-    if (x > cc.b) {
-        e.right += g;
-        return 0.0f;
-    }
-    const int c = cell_of(x, cc.inv_w, cc.off, K);
+    const float xc = fminf(fmaxf(x, cc.a), cc.b);  // NaN -> a
+    const int c = cell_of(xc, cc.inv_w, cc.off, K);
     const float2 r = sP[c * kCh + ch];
     const uint32_t bits = __float_as_uint(r.x);
-    int i;
-    float delta, one_minus;
-    float2 q;
-    if ((bits & 0xFFC00000u) != kLinkTag) {  // inside interval i: {i, x_{i-1}}
-        i = __float_as_int(r.x);
-        q = sI[i * kCh + ch];
-        delta = (x - r.y) * q.y;
-        one_minus = 1.0f - delta;
-    } else {
-        int k = (int)(bits & kKnotTagMask);
-        float xk = r.y;
-        if (CHAINS && (bits & kKnotTagChain)) {
-            for (int gg = 0; gg < cc.max_chain && k < N; ++gg) {
-                const float xn = xs[(k + 1) * kCh + ch];
-                if (!(x >= xn)) break;
-                ++k;
-                xk = xn;
-            }
-        }
-        if (x < xk) {  // interval k, measured from its right end
-            i = k;
-            q = sI[i * kCh + ch];
-            one_minus = (xk - x) * q.y;
-            delta = 1.0f - one_minus;
-        } else if (k < N) {
-            i = k + 1;
-            q = sI[i * kCh + ch];
-            delta = (x - xk) * q.y;
-            one_minus = 1.0f - delta;
-        } else {  // x == x_N
-            i = N;
-            q = sI[i * kCh + ch];
-            delta = 1.0f;
-            one_minus = 0.0f;
+    const bool knot = (bits & 0xFFC00000u) == kLinkTag;
+    int k = knot ? (int)(bits & kKnotTagMask) : __float_as_int(r.x) - 1;
+    float xk = r.y;
+    if (CHAINS && knot && (bits & kKnotTagChain)) {
+        for (int gg = 0; gg < cc.max_chain && k < N; ++gg) {
+            const float xn = xs[(k + 1) * kCh + ch];
+            if (!(xc >= xn)) break;
+            ++k;
+            xk = xn;
         }
     }
-    atomicAdd(accA + i * kCh + ch, g * one_minus);
-    atomicAdd(accB + i * kCh + ch, g * delta);
-    return g * q.x;
+    // right of x_k: interval k + 1 from its left end; left of it: interval k
+    // from its right end; x = x_N: interval N at delta = 1
+    const bool right = xc >= xk;
+    const bool at_b = right && k == N;
+    const int i = right && !at_b ? k + 1 : k;
+    const float2 q = sI[i * kCh + ch];
+    const float tt = (right ? (xc - xk) : (xk - xc)) * q.y;
+    const float delta = at_b ? 1.0f : (right ? tt : 1.0f - tt);
+    const float one_minus = at_b ? 0.0f : (right ? 1.0f - tt : tt);
+    const bool inside = x >= cc.a && x <= cc.b;  // false for NaN
+    if (inside) {
+        atomicAdd(accA + i * kCh + ch, g * one_minus);
+        atomicAdd(accB + i * kCh + ch, g * delta);
+    }
+    e.left += x < cc.a ? g : 0.0f;
+    e.right += x > cc.b ? g : 0.0f;
+    const float gx = inside ? g * q.x : 0.0f;
+    return x != x ? x : gx;
 }
 
 template <bool CHAINS>
