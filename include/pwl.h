@@ -365,14 +365,15 @@ pwl_status pwl_batch_get_info(pwl_batch b, pwl_batch_info* info);
 /* y[r, c] = v_c(x[r, c]) for a row-major x[rows, n_channels], where channel
  * c is the CPWL function with FP32 knots d_knots[c, 0..N] and values
  * d_values[c, 0..N] (device arrays [n_channels, N+1], e.g. learnable
- * parameters).  Each CTA builds the cell index of 16 channels in shared
- * memory (k_cells cells per channel, 0 selects 4 (N+1); cells holding
- * several knots are walked).  io_dtype PWL_FP32 or PWL_BF16 (x and y alike);
- * the arithmetic is FP32; clamping and NaN as in pwl_eval.  Knots must be
- * strictly increasing per channel: a violation sets bit 0 of the device
- * word *d_status (the caller zeroes it; results are then unspecified).
- * Errors: PWL_ENOTSUP if 16 channels' index does not fit a CTA
- * (16 (8 (k_cells + 2 (N+1)) + 4 (N+1)) bytes).                          */
+ * parameters).  Each CTA builds the cell index of 8 channels in shared
+ * memory (k_cells cells per channel of 16 bytes each, 0 selects 4 (N+1) as
+ * far as the CTA's shared memory allows; cells holding several knots are
+ * walked).  io_dtype PWL_FP32 or PWL_BF16 (x and y alike); the arithmetic
+ * is FP32; clamping and NaN as in pwl_eval.  Knots must be strictly
+ * increasing per channel: a violation sets bit 0 of the device word
+ * *d_status (the caller zeroes it; results are then unspecified).
+ * Errors: PWL_ENOTSUP if 8 channels' index does not fit a CTA
+ * (128 (k_cells + N + 1) bytes).                                           */
 pwl_status pwl_channels_forward(const float* d_knots, const float* d_values, int64_t n_channels,
                                 int64_t n_intervals, int64_t k_cells, const void* d_x, void* d_y,
                                 int64_t rows, int32_t io_dtype, int32_t* d_status, void* stream);

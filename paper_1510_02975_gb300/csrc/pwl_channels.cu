@@ -63,15 +63,14 @@ __device__ __forceinline__ int lower_bound_cells(const int* cj, int n, int v)
 // ~2^-23 |v_i - v_{i-1}| (FP64 would cost a slow FP64 division per record on
 // this GPU's few FP64 units).
 
-// Builds the index of channels [c0, c0 + 16) in shared memory.
-//   sP[cell * 16 + ch]      cell records
-//   sX[e * 16 + ch]         forward: side records e = 2k + side (2 (N+1));
-//                           backward: interval records e = i (N+2)
+// Builds the backward index of channels [c0, c0 + 16) in shared memory.
+//   sP[cell * 16 + ch]      cell records {i, x_{i-1}} or {knot tag, x_k}
+//   sX[i * 16 + ch]         interval records {s_i, 1/h_i}, i = 0..N+1 (0 and N+1
+//                           copy intervals 1 and N)
 //   xs[j * 16 + ch]         the tile's knots (staged first, coalesced)
 //   cj[j * 16 + ch]         scratch: first the tile's values, then the cell of knot j
 // Every global read is a coalesced pass over the tile's knots and values;
 // the rest works in shared memory.
-template <bool BWD>
 __device__ void build_tile(const ChanArgs& p, int64_t c0, float2* sP, float2* sX, float* xs, int* cj,
                            TileParams* tp)
 {
@@ -106,22 +105,12 @@ __device__ void build_tile(const ChanArgs& p, int64_t c0, float2* sP, float2* sX
         tp->w[ch] = (b - a) / (float)K;
         tp->max_chain[ch] = 0;
     }
-    // side (forward) or interval (backward) records, from the staged arrays
-    const int nx = BWD ? (N + 2) : 2 * n1;
-    for (int e = threadIdx.x; e < nx * kCh; e += blockDim.x) {
+    // interval records, from the staged arrays
+    for (int e = threadIdx.x; e < (N + 2) * kCh; e += blockDim.x) {
         const int q = e / kCh, ch = e % kCh;
-        float2 rec;
-        if (BWD) {  // interval q (0 and N+1 copy 1 and N)
-            const int i = min(max(q, 1), N);
-            const float h = __fsub_rn(xs[i * kCh + ch], xs[(i - 1) * kCh + ch]);
-            rec = make_float2(__fdiv_rn(__fsub_rn(vs[i * kCh + ch], vs[(i - 1) * kCh + ch]), h), __frcp_rn(h));
-        } else {    // side record of knot k = q / 2
-            const int k = q >> 1;
-            const int i = (q & 1) ? min(k + 1, N) : max(k, 1);
-            const float h = __fsub_rn(xs[i * kCh + ch], xs[(i - 1) * kCh + ch]);
-            rec = make_float2(vs[k * kCh + ch], __fdiv_rn(__fsub_rn(vs[i * kCh + ch], vs[(i - 1) * kCh + ch]), h));
-        }
-        sX[e] = rec;
+        const int i = min(max(q, 1), N);  // interval q (0 and N+1 copy 1 and N)
+        const float h = __fsub_rn(xs[i * kCh + ch], xs[(i - 1) * kCh + ch]);
+        sX[e] = make_float2(__fdiv_rn(__fsub_rn(vs[i * kCh + ch], vs[(i - 1) * kCh + ch]), h), __frcp_rn(h));
     }
     __syncthreads();
     // cells of the knots (overwrites the staged values)
@@ -148,16 +137,9 @@ __device__ void build_tile(const ChanArgs& p, int64_t c0, float2* sP, float2* sX
         if (lb <= N && cj[lb * kCh + ch] == c) {
             const bool chain = (lb < N && cj[(lb + 1) * kCh + ch] == c);
             rec = make_float2(make_knot_tag(lb, chain), xs[lb * kCh + ch]);
-        } else if (BWD) {
+        } else {
             const int i = lb;  // the cell lies inside interval i = [x_{i-1}, x_i]
             rec = make_float2(__int_as_float(i), xs[(i - 1) * kCh + ch]);
-        } else {
-            // the line of interval j+1 through (x_j, v_j): {v_j, s_{j+1}} is the
-            // right side record of knot j; valued at the anchor x_c
-            const int j = lb - 1;
-            const float2 sr = sX[(2 * j + 1) * kCh + ch];
-            const float xc = __fmaf_rn(__int2float_rn(c), tp->w[ch], tp->a[ch]);
-            rec = make_float2(__fmaf_rn(__fsub_rn(xc, xs[j * kCh + ch]), sr.y, sr.x), sr.y);
         }
         sP[e] = rec;
     }
@@ -173,33 +155,6 @@ struct ChanConst {
     {
     }
 };
-
-template <bool CHAINS>
-__device__ __forceinline__ float chan_fwd_one(float x, int ch, const float* __restrict__ xs, const float2* sP,
-                                              const float2* sS, const ChanConst& cc, int N, int K)
-{
-    const float xc = clamp_nan(x, cc.a, cc.b);
-    const int c = cell_of(xc, cc.inv_w, cc.off, K);
-    const float2 r = sP[c * kCh + ch];
-    const uint32_t bits = __float_as_uint(r.x);
-    float anchor = __fmaf_rn(__int2float_rn(c), cc.w, cc.a);
-    float2 q = r;
-    if ((bits & 0xFFC00000u) == kLinkTag) {
-        int k = (int)(bits & kKnotTagMask);
-        float xk = r.y;
-        if (CHAINS && (bits & kKnotTagChain)) {
-            for (int g = 0; g < cc.max_chain && k < N; ++g) {
-                const float xn = xs[(k + 1) * kCh + ch];
-                if (!(xc >= xn)) break;
-                ++k;
-                xk = xn;
-            }
-        }
-        q = sS[(2 * k + (xc >= xk ? 1 : 0)) * kCh + ch];
-        anchor = xk;
-    }
-    return __fmaf_rn(xc - anchor, q.y, q.x);
-}
 
 template <typename IO>
 __device__ __forceinline__ float to_f32(IO v);
@@ -217,60 +172,210 @@ __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { retu
 __device__ __forceinline__ void st_cs(float* p, float v) { __stcs(p, v); }
 __device__ __forceinline__ void st_cs(__nv_bfloat16* p, __nv_bfloat16 v) { *p = v; }
 
-template <typename IO, bool CHAINS>
-__device__ __forceinline__ void chan_fwd_rows(const ChanArgs& p, int64_t c0, int64_t r0, int64_t r1,
-                                              const float2* sP, const float2* sS, const float* xs,
-                                              const TileParams& tp, const IO* __restrict__ x, IO* __restrict__ y)
-{
-    const int ch = threadIdx.x % kCh;
-    const int64_t c = c0 + ch;
-    if (c >= p.C) return;
-    const ChanConst cc(tp, ch);
-    int64_t r = r0 + threadIdx.x / kCh;
-    const int64_t pass = (int64_t)kRowsPerPass * p.C;  // elements between a thread's consecutive rows
-    const IO* px = x + r * p.C + c;
-    IO* py = y + r * p.C + c;
-    for (; r + (int64_t)(kChUnroll - 1) * kRowsPerPass < r1; r += (int64_t)kChUnroll * kRowsPerPass) {
-        float v[kChUnroll];
-#pragma unroll
-        for (int u = 0; u < kChUnroll; ++u) v[u] = to_f32<IO>(px[u * pass]);
-#pragma unroll
-        for (int u = 0; u < kChUnroll; ++u) v[u] = chan_fwd_one<CHAINS>(v[u], ch, xs, sP, sS, cc, p.N, p.K);
-#pragma unroll
-        for (int u = 0; u < kChUnroll; ++u) st_cs(py + u * pass, from_f32<IO>(v[u]));
-        px += kChUnroll * pass;
-        py += kChUnroll * pass;
+// ---- forward: 8-channel tiles with 16-byte split records ---------------------
+// A cell record is {x_s, y_s, s_left, s_right}: v(x) = y_s + (x - x_s) s with
+// s = s_left left of x_s and s_right from x_s on.  A knot-free cell inside
+// interval i stores its anchor x_c = a + c w, the line's value there and s_i
+// twice; a cell holding one knot k stores {x_k, v_k, s_k, s_{k+1}}.  One
+// 16-byte load, a compare, a select and an FMA per element; no tag test and
+// no second load.  A cell holding several knots stores a NaN-tagged s_right
+// (knot k, its first): elements right of x_k walk the tile's knots and take
+// {x_k', v_k', s_{k'+1}} from the staged knots, values and slopes.
+// Records are channel-interleaved ([c * 8 + ch]): the 8 lanes of a quarter
+// warp read 8 different 16-byte bank groups.  With 4 cells per knot a tile
+// takes 128 (K + N + 1) bytes (164 KB at N = 256), so a CTA owns 8 channels,
+// and 4-CTA clusters walk the same rows at once to use whole 128-byte lines.
+constexpr int kChF = 8;                           // channels per forward tile
+constexpr int kClF = 4;                           // CTAs per forward cluster (32 channels)
+constexpr int kRowsPerPassF = kChThreads / kChF;  // 128 rows per pass
+constexpr int kChUnrollF = 16;
+
+struct TileParamsF {
+    float a[kChF], b[kChF], inv_w[kChF], off[kChF], w[kChF];
+    int max_chain[kChF];
+    int any_chain;
+    int bad;
+};
+
+struct ChanConstF {
+    float a, b, inv_w, off, w;
+    int max_chain;
+    __device__ __forceinline__ ChanConstF(const TileParamsF& tp, int ch)
+        : a(tp.a[ch]), b(tp.b[ch]), inv_w(tp.inv_w[ch]), off(tp.off[ch]), w(tp.w[ch]), max_chain(tp.max_chain[ch])
+    {
     }
-    for (; r < r1; r += kRowsPerPass, px += pass, py += pass)
-        *py = from_f32<IO>(chan_fwd_one<CHAINS>(to_f32<IO>(*px), ch, xs, sP, sS, cc, p.N, p.K));
+};
+
+__device__ __forceinline__ int lower_bound_cells8(const int* cj, int n, int v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cj[mid * kChF] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
+// Builds the forward index of channels [c0, c0 + 8) in shared memory:
+//   R[c * 8 + ch]   cell records (K)
+//   xs, vs, sp      knots, values and slopes s_{j+1} (s_N for j = N), [j * 8 + ch]
+//   cj              build scratch: the cell of knot j
+__device__ void build_tile_fwd(const ChanArgs& p, int64_t c0, float4* R, float* xs, float* vs, float* sp, int* cj,
+                               TileParamsF* tp)
+{
+    const int N = p.N, K = p.K, n1 = N + 1;
+    const int nch = (int)min((int64_t)kChF, p.C - c0);
+    for (int e = threadIdx.x; e < kChF * n1; e += blockDim.x) {
+        const int ch = e / n1, j = e % n1;  // j fastest: coalesced reads of each channel's row
+        float xv, vv;
+        if (ch < nch) {
+            xv = p.knots[(c0 + ch) * (int64_t)n1 + j];
+            vv = p.values[(c0 + ch) * (int64_t)n1 + j];
+        } else {  // padding channel of a partial tile: an unused identity on [0, 1]
+            xv = (float)j / (float)N;
+            vv = 0.0f;
+        }
+        xs[j * kChF + ch] = xv;
+        vs[j * kChF + ch] = vv;
+    }
+    if (threadIdx.x == 0) {
+        tp->any_chain = 0;
+        tp->bad = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < kChF) {
+        const int ch = threadIdx.x;
+        const float a = xs[ch], b = xs[N * kChF + ch];
+        tp->a[ch] = a;
+        tp->b[ch] = b;
+        tp->inv_w[ch] = (float)K / (b - a);
+        tp->off[ch] = -a * tp->inv_w[ch];
+        tp->w[ch] = (b - a) / (float)K;
+        tp->max_chain[ch] = 0;
+    }
+    for (int e = threadIdx.x; e < n1 * kChF; e += blockDim.x) {
+        const int j = e / kChF, ch = e % kChF;
+        const int i = min(j + 1, N);  // slope of interval j + 1 (of interval N for j = N)
+        const float h = __fsub_rn(xs[i * kChF + ch], xs[(i - 1) * kChF + ch]);
+        sp[e] = __fdiv_rn(__fsub_rn(vs[i * kChF + ch], vs[(i - 1) * kChF + ch]), h);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n1 * kChF; e += blockDim.x) {
+        const int j = e / kChF, ch = e % kChF;
+        const float xj = xs[e];
+        if (j > 0 && !(xj > xs[e - kChF])) atomicOr(&tp->bad, 1);
+        cj[e] = cell_of(xj, tp->inv_w[ch], tp->off[ch], K);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n1 * kChF; e += blockDim.x) {
+        const int j = e / kChF, ch = e % kChF;
+        if (j > 0 && cj[e] == cj[e - kChF]) {
+            int first = j;
+            while (first > 0 && cj[(first - 1) * kChF + ch] == cj[e]) --first;
+            atomicMax(&tp->max_chain[ch], j - first);
+            atomicOr(&tp->any_chain, 1);
+        }
+    }
+    for (int e = threadIdx.x; e < K * kChF; e += blockDim.x) {
+        const int c = e / kChF, ch = e % kChF;
+        const int lb = lower_bound_cells8(cj + ch, n1, c);
+        float4 rec;
+        if (lb <= N && cj[lb * kChF + ch] == c) {  // knot lb is the cell's first knot
+            const int k = lb;
+            const bool chain = k < N && cj[(k + 1) * kChF + ch] == c;
+            const float sl = sp[max(k - 1, 0) * kChF + ch];
+            const float sr = chain ? make_knot_tag(k, true) : sp[k * kChF + ch];
+            rec = make_float4(xs[k * kChF + ch], vs[k * kChF + ch], sl, sr);
+        } else {  // inside interval lb: the line through (x_j, v_j), j = lb - 1, at the anchor
+            const int j = lb - 1;
+            const float sj = sp[j * kChF + ch];
+            const float xc = __fmaf_rn(__int2float_rn(c), tp->w[ch], tp->a[ch]);
+            rec = make_float4(xc, __fmaf_rn(__fsub_rn(xc, xs[j * kChF + ch]), sj, vs[j * kChF + ch]), sj, sj);
+        }
+        R[e] = rec;
+    }
+    __syncthreads();
+}
+
+template <bool CHAINS>
+__device__ __forceinline__ float chan_fwd8(float x, int ch, const float4* R, const float* xs, const float* vs,
+                                           const float* sp, const ChanConstF& cc, int N, int K)
+{
+    const float xc = clamp_nan(x, cc.a, cc.b);
+    const int c = cell_of(xc, cc.inv_w, cc.off, K);
+    const float4 r = R[c * kChF + ch];
+    float s = xc < r.x ? r.z : r.w;
+    float anchor = r.x, y0 = r.y;
+    if (CHAINS && s != s) {  // right of the first knot of a cell holding several
+        int k = (int)(__float_as_uint(r.w) & kKnotTagMask);
+        for (int g = 0; g < cc.max_chain && k < N; ++g) {
+            if (!(xc >= xs[(k + 1) * kChF + ch])) break;
+            ++k;
+        }
+        anchor = xs[k * kChF + ch];
+        y0 = vs[k * kChF + ch];
+        s = sp[k * kChF + ch];
+    }
+    return __fmaf_rn(xc - anchor, s, y0);
+}
+
+template <typename IO, bool CHAINS>
+__device__ __forceinline__ void chan_fwd8_rows(const ChanArgs& p, int64_t c0, int64_t r0, int64_t r1,
+                                               const float4* R, const float* xs, const float* vs, const float* sp,
+                                               const TileParamsF& tp, const IO* __restrict__ x, IO* __restrict__ y)
+{
+    const int ch = threadIdx.x % kChF;
+    const int64_t c = c0 + ch;
+    if (c >= p.C) return;
+    const ChanConstF cc(tp, ch);
+    int64_t r = r0 + threadIdx.x / kChF;
+    const int64_t pass = (int64_t)kRowsPerPassF * p.C;  // elements between a thread's consecutive rows
+    const IO* px = x + r * p.C + c;
+    IO* py = y + r * p.C + c;
+    for (; r + (int64_t)(kChUnrollF - 1) * kRowsPerPassF < r1; r += (int64_t)kChUnrollF * kRowsPerPassF) {
+        float v[kChUnrollF];
+#pragma unroll
+        for (int u = 0; u < kChUnrollF; ++u) v[u] = to_f32<IO>(px[u * pass]);
+#pragma unroll
+        for (int u = 0; u < kChUnrollF; ++u) v[u] = chan_fwd8<CHAINS>(v[u], ch, R, xs, vs, sp, cc, p.N, p.K);
+#pragma unroll
+        for (int u = 0; u < kChUnrollF; ++u) st_cs(py + u * pass, from_f32<IO>(v[u]));
+        px += kChUnrollF * pass;
+        py += kChUnrollF * pass;
+    }
+    for (; r < r1; r += kRowsPerPassF, px += pass, py += pass)
+        *py = from_f32<IO>(chan_fwd8<CHAINS>(to_f32<IO>(*px), ch, R, xs, vs, sp, cc, p.N, p.K));
+}
+
+// Units = (tile quad, chunk of rows), quad-major; the 4 CTAs of a cluster take
+// the 4 tiles of a quad on the same rows.
 template <typename IO>
 __global__ void __launch_bounds__(kChThreads, 1) channels_forward_kernel(const ChanArgs p, const IO* x, IO* y)
 {
     extern __shared__ float4 s_ch[];
-    float2* sP = reinterpret_cast<float2*>(s_ch);
-    float2* sS = sP + (size_t)p.K * kCh;
-    float* xs = reinterpret_cast<float*>(sS + (size_t)2 * (p.N + 1) * kCh);
-    int* cj = reinterpret_cast<int*>(xs + (size_t)(p.N + 1) * kCh);
-    __shared__ TileParams tp;
-    const int64_t cluster = blockIdx.x >> 1, nclusters = gridDim.x >> 1;
+    float4* R = s_ch;
+    float* xs = reinterpret_cast<float*>(R + (size_t)p.K * kChF);
+    float* vs = xs + (size_t)(p.N + 1) * kChF;
+    float* sp = vs + (size_t)(p.N + 1) * kChF;
+    int* cj = reinterpret_cast<int*>(sp + (size_t)(p.N + 1) * kChF);
+    __shared__ TileParamsF tp;
+    const int64_t cluster = blockIdx.x / kClF, nclusters = gridDim.x / kClF;
     const int64_t u0 = p.units * cluster / nclusters, u1 = p.units * (cluster + 1) / nclusters;
     int64_t built = -1;
     for (int64_t u = u0; u < u1; ++u) {
-        const int64_t tile = 2 * (u / p.per_pair) + (blockIdx.x & 1), chunk = u % p.per_pair;
-        if (tile >= p.tiles) break;  // the odd tile out of an odd tile count
+        const int64_t tile = kClF * (u / p.per_pair) + (blockIdx.x % kClF), chunk = u % p.per_pair;
+        if (tile >= p.tiles) continue;  // a tile past the last one of a partial quad
         if (tile != built) {
             __syncthreads();
-            build_tile<false>(p, tile * kCh, sP, sS, xs, cj, &tp);
+            build_tile_fwd(p, tile * kChF, R, xs, vs, sp, cj, &tp);
             if (threadIdx.x == 0 && tp.bad) atomicOr(p.status, 1);
             built = tile;
         }
         const int64_t r0 = chunk * p.rows_per_unit, r1 = min(p.R, r0 + p.rows_per_unit);
         if (tp.any_chain)
-            chan_fwd_rows<IO, true>(p, tile * kCh, r0, r1, sP, sS, xs, tp, x, y);
+            chan_fwd8_rows<IO, true>(p, tile * kChF, r0, r1, R, xs, vs, sp, tp, x, y);
         else
-            chan_fwd_rows<IO, false>(p, tile * kCh, r0, r1, sP, sS, xs, tp, x, y);
+            chan_fwd8_rows<IO, false>(p, tile * kChF, r0, r1, R, xs, vs, sp, tp, x, y);
     }
 }
 
@@ -421,7 +526,7 @@ __global__ void __launch_bounds__(kChThreads, 1) channels_backward_kernel(const 
         if (tile != built) {
             if (built >= 0) flush_tile(p, built * kCh, sI, accA, accB, g_values, g_knots);
             __syncthreads();
-            build_tile<true>(p, tile * kCh, sP, sI, xs, cj, &tp);
+            build_tile(p, tile * kCh, sP, sI, xs, cj, &tp);
             if (threadIdx.x == 0 && tp.bad) atomicOr(p.status, 1);
             for (int e = threadIdx.x; e < (p.N + 2) * kCh; e += blockDim.x) {
                 accA[e] = 0.0f;
@@ -444,9 +549,10 @@ __global__ void __launch_bounds__(kChThreads, 1) channels_backward_kernel(const 
 size_t channels_smem_bytes(int64_t N, int64_t K, bool backward)
 {
     const size_t n1 = (size_t)(N + 1), n2 = (size_t)(N + 2);
-    const size_t knots = sizeof(float) * kCh * n1;  // staged knots
-    if (!backward) return sizeof(float2) * kCh * ((size_t)K + 2 * n1) + 2 * knots;  // + values / cells
-    return sizeof(float2) * kCh * ((size_t)K + n2) + sizeof(float) * 2 * kCh * n2 + knots;
+    // forward: 8 channels of 16-byte cell records, knots, values, slopes and build scratch
+    if (!backward) return sizeof(float4) * kChF * (size_t)K + 4 * sizeof(float) * kChF * n1;
+    // backward: 16 channels of 8-byte cell and interval records, two accumulators, knots
+    return sizeof(float2) * kCh * ((size_t)K + n2) + sizeof(float) * 2 * kCh * n2 + sizeof(float) * kCh * n1;
 }
 
 int64_t channels_default_cells(int64_t N, bool backward)
@@ -464,11 +570,13 @@ pwl_status channels_launch(const ChanArgs& base, bool backward, int io_dtype, co
     ChanArgs p = base;
     const size_t smem = channels_smem_bytes(p.N, p.K, backward);
     const DeviceInfo& di = device_info();
+    const int tile_ch = backward ? kCh : kChF;       // channels per tile
+    const int cluster_ctas = backward ? 2 : kClF;    // CTAs per cluster (adjacent tiles, same rows)
     if (smem > di.smem_optin)
-        return fail(PWL_ENOTSUP, "channel index of %zu bytes (16 channels x %d cells, N = %d) does not fit one CTA",
-                    smem, p.K, p.N);
-    p.tiles = (p.C + kCh - 1) / kCh;
-    const int64_t pairs = (p.tiles + 1) / 2;
+        return fail(PWL_ENOTSUP, "channel index of %zu bytes (%d channels x %d cells, N = %d) does not fit one CTA",
+                    smem, tile_ch, p.K, p.N);
+    p.tiles = (p.C + tile_ch - 1) / tile_ch;
+    const int64_t pairs = (p.tiles + cluster_ctas - 1) / cluster_ctas;  // tile groups of one cluster
     const void* kfn;
     if (backward)
         kfn = (const void*)channels_backward_kernel;
@@ -480,7 +588,7 @@ pwl_status channels_launch(const ChanArgs& base, bool backward, int io_dtype, co
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = cluster_ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(kChThreads);
@@ -488,20 +596,20 @@ pwl_status channels_launch(const ChanArgs& base, bool backward, int io_dtype, co
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cfg.gridDim = dim3(2);
+    cfg.gridDim = dim3(cluster_ctas);
     int clusters = 0;
     PWL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg));
     clusters = std::max(clusters, 1);
     // about 8 units per cluster: few index builds per CTA, and the last
     // units balance the load
     int64_t chunks = std::max<int64_t>(1, ((int64_t)clusters * 8 + pairs - 1) / pairs);
-    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, p.R / kRowsPerPass));
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, p.R / (kChThreads / tile_ch)));
     p.rows_per_unit = (p.R + chunks - 1) / chunks;
     chunks = (p.R + p.rows_per_unit - 1) / p.rows_per_unit;
     p.per_pair = chunks;
     p.units = pairs * chunks;
     clusters = (int)std::min<int64_t>(clusters, p.units);
-    cfg.gridDim = dim3(2 * clusters);
+    cfg.gridDim = dim3(cluster_ctas * clusters);
     if (backward) {
         PWL_CUDA_TRY(cudaLaunchKernelEx(&cfg, channels_backward_kernel, p, static_cast<const float*>(x), gy, gx,
                                         g_values, g_knots));
