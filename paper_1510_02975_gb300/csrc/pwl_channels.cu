@@ -5,27 +5,23 @@
 // arrays [C, N+1] (learnable parameters that change every step), so each CTA
 // builds the cell index of its channels in shared memory when it starts.
 //
-// Layout: a CTA owns a tile of 16 consecutive channels; a warp covers two
-// rows of the tile (lane = row_half * 16 + channel), so every global access
-// is a 64-byte row segment and the 16 lanes of a half-warp always address 16
-// different channels.  The per-channel indexes are stored channel-interleaved
-// (entry e of channel ch at [e * 16 + ch]), so a half-warp's shared-memory
-// accesses hit 16 different banks whatever cells or knots they look up.
+// Forward: a CTA owns a tile of 8 consecutive channels and keeps, per
+// channel, 16-byte cell records {x_s, y_s, s_left, s_right} (one load, a
+// compare, a select and an FMA per element), channel-interleaved ([c * 8 + ch])
+// so that the 8 lanes of a quarter warp read 8 different bank groups.  Four
+// CTAs form a thread-block cluster on adjacent tiles (32 channels, 128-byte
+// row segments) and walk the same rows at once.
 //
-// Forward index per channel: the 8-byte cell index of the single-table path
-// (cell records {y_c, s} or {knot tag, x_k}; side records {v_k, s_k},
-// {v_k, s_{k+1}}).  Backward index per channel: cell records {i, x_{i-1}}
-// for cells inside interval i or {knot tag, x_k}; interval records
-// {s_i, 1/h_i}.
+// Backward: a CTA owns 16 channels (a warp covers two rows, 64-byte row
+// segments), with 8-byte cell records {i, x_{i-1}} or {knot tag, x_k} and
+// interval records {s_i, 1/h_i}, channel-interleaved ([e * 16 + ch]), and
+// two shared accumulators per interval; 2-CTA clusters (128-byte segments).
 //
-// Work: the grid is made of 2-CTA clusters; a cluster takes a pair of
-// adjacent tiles (32 channels, 128-byte row segments) and its two CTAs walk
-// the same rows at the same time, one tile each, so that the two halves of
-// every 128-byte line of x are read while it is in L2 (one CTA alone would
-// leave the other half to a CTA that reads it much later, and the line would
-// be fetched twice).  Units = (tile pair, chunk of rows), pair-major; each
-// cluster takes a contiguous range of units and rebuilds its indexes only
-// when the pair changes.
+// Both: the rows of x are split into chunks; units = (tile group, chunk of
+// rows), group-major; each cluster takes a contiguous range of units and
+// rebuilds its indexes only when the group changes.  A 32-byte row segment
+// read by one CTA alone costs a whole line fetch; the sibling CTAs of a
+// cluster use the rest of the line while it is in L2.
 #include <math.h>
 
 #include <algorithm>
@@ -40,6 +36,7 @@ constexpr int kCh = 16;  // channels per tile
 constexpr int kChThreads = 1024;
 constexpr int kRowsPerPass = kChThreads / kCh;  // 64 rows per pass of the CTA
 constexpr int kChUnroll = 16;                    // passes in flight per thread (64 KB per SM)
+constexpr int kChTail = 3;
 
 struct TileParams {
     float a[kCh], b[kCh], inv_w[kCh], off[kCh], w[kCh];
@@ -188,7 +185,8 @@ __device__ __forceinline__ void st_cs(__nv_bfloat16* p, __nv_bfloat16 v) { *p = 
 constexpr int kChF = 8;                           // channels per forward tile
 constexpr int kClF = 4;                           // CTAs per forward cluster (32 channels)
 constexpr int kRowsPerPassF = kChThreads / kChF;  // 128 rows per pass
-constexpr int kChUnrollF = 16;
+constexpr int kChUnrollF = 24;
+constexpr int kChTailF = 8;
 
 struct TileParamsF {
     float a[kChF], b[kChF], inv_w[kChF], off[kChF], w[kChF];
@@ -343,8 +341,21 @@ __device__ __forceinline__ void chan_fwd8_rows(const ChanArgs& p, int64_t c0, in
         px += kChUnrollF * pass;
         py += kChUnrollF * pass;
     }
-    for (; r < r1; r += kRowsPerPassF, px += pass, py += pass)
-        *py = from_f32<IO>(chan_fwd8<CHAINS>(to_f32<IO>(*px), ch, R, xs, vs, sp, cc, p.N, p.K));
+    // the rest (fewer than kChUnrollF rows per thread) in predicated batches of
+    // kChTailF: a few load latencies instead of one per row
+    for (; r < r1; r += (int64_t)kChTailF * kRowsPerPassF) {
+        const int64_t left = (r1 - r + kRowsPerPassF - 1) / kRowsPerPassF;
+        const int rem = left < kChTailF ? (int)left : kChTailF;
+        float v[kChTailF];
+#pragma unroll
+        for (int u = 0; u < kChTailF; ++u)
+            if (u < rem) v[u] = to_f32<IO>(px[u * pass]);
+#pragma unroll
+        for (int u = 0; u < kChTailF; ++u)
+            if (u < rem) st_cs(py + u * pass, from_f32<IO>(chan_fwd8<CHAINS>(v[u], ch, R, xs, vs, sp, cc, p.N, p.K)));
+        px += kChTailF * pass;
+        py += kChTailF * pass;
+    }
 }
 
 // Units = (tile quad, chunk of rows), quad-major; the 4 CTAs of a cluster take
@@ -468,8 +479,26 @@ __device__ __forceinline__ void chan_bwd_rows(const ChanArgs& p, int64_t c0, int
             pg += U * pass;
             po += U * pass;
         }
-        for (; r < r1; r += kRowsPerPass, px += pass, pg += pass, po += pass)
-            *po = chan_bwd_one<CHAINS>(*px, *pg, ch, xs, sP, sI, cc, p.N, p.K, accA, accB, e);
+        // the rest (fewer than U rows per thread) in predicated batches of
+        // kChTail: a few load latencies instead of one per row
+        for (; r < r1; r += (int64_t)kChTail * kRowsPerPass) {
+            const int64_t left = (r1 - r + kRowsPerPass - 1) / kRowsPerPass;
+            const int rem = left < kChTail ? (int)left : kChTail;
+            float xv[kChTail], gv[kChTail];
+#pragma unroll
+            for (int u = 0; u < kChTail; ++u)
+                if (u < rem) {
+                    xv[u] = px[u * pass];
+                    gv[u] = pg[u * pass];
+                }
+#pragma unroll
+            for (int u = 0; u < kChTail; ++u)
+                if (u < rem)
+                    po[u * pass] = chan_bwd_one<CHAINS>(xv[u], gv[u], ch, xs, sP, sI, cc, p.N, p.K, accA, accB, e);
+            px += kChTail * pass;
+            pg += kChTail * pass;
+            po += kChTail * pass;
+        }
     }
     // lanes ch and ch + 16 share a channel: one add each
     if (e.left != 0.0f) atomicAdd(accA + 0 * kCh + ch, e.left);
