@@ -74,8 +74,9 @@ __device__ void build_tile(const ChanArgs& p, int64_t c0, float2* sP, float2* sX
     const int N = p.N, K = p.K, n1 = N + 1;
     const int nch = (int)min((int64_t)kCh, p.C - c0);
     float* vs = reinterpret_cast<float*>(cj);
-    for (int e = threadIdx.x; e < kCh * n1; e += blockDim.x) {
-        const int ch = e / n1, j = e % n1;  // j fastest: consecutive threads read consecutive knots
+    const int per_ch = blockDim.x / kCh;  // threads per channel
+    for (int ch = threadIdx.x / per_ch, j = threadIdx.x % per_ch; j < n1; j += per_ch) {
+        // consecutive threads read consecutive knots of one channel
         float xv, vv;
         if (ch < nch) {
             xv = p.knots[(c0 + ch) * (int64_t)n1 + j];
@@ -127,18 +128,25 @@ __device__ void build_tile(const ChanArgs& p, int64_t c0, float2* sP, float2* sX
             atomicOr(&tp->any_chain, 1);
         }
     }
-    for (int e = threadIdx.x; e < K * kCh; e += blockDim.x) {
-        const int c = e / kCh, ch = e % kCh;
-        const int lb = lower_bound_cells(cj + ch, n1, c);
-        float2 rec;
-        if (lb <= N && cj[lb * kCh + ch] == c) {
-            const bool chain = (lb < N && cj[(lb + 1) * kCh + ch] == c);
-            rec = make_float2(make_knot_tag(lb, chain), xs[lb * kCh + ch]);
-        } else {
-            const int i = lb;  // the cell lies inside interval i = [x_{i-1}, x_i]
-            rec = make_float2(__int_as_float(i), xs[(i - 1) * kCh + ch]);
+    // cell records: each thread takes a run of consecutive cells of one
+    // channel, finds the first one's knot by bisection and walks on
+    {
+        const int ch = threadIdx.x % kCh, runs = blockDim.x / kCh, q = threadIdx.x / kCh;
+        const int per = (K + runs - 1) / runs;
+        const int cb = q * per, ce = min(K, cb + per);
+        int lb = cb < ce ? lower_bound_cells(cj + ch, n1, cb) : 0;
+        for (int c = cb; c < ce; ++c) {
+            while (lb < n1 && cj[lb * kCh + ch] < c) ++lb;  // lb: the first knot whose cell is >= c
+            float2 rec;
+            if (lb <= N && cj[lb * kCh + ch] == c) {
+                const bool chain = (lb < N && cj[(lb + 1) * kCh + ch] == c);
+                rec = make_float2(make_knot_tag(lb, chain), xs[lb * kCh + ch]);
+            } else {
+                const int i = lb;  // the cell lies inside interval i = [x_{i-1}, x_i]
+                rec = make_float2(__int_as_float(i), xs[(i - 1) * kCh + ch]);
+            }
+            sP[c * kCh + ch] = rec;
         }
-        sP[e] = rec;
     }
     __syncthreads();
 }
@@ -223,8 +231,9 @@ __device__ void build_tile_fwd(const ChanArgs& p, int64_t c0, float4* R, float* 
 {
     const int N = p.N, K = p.K, n1 = N + 1;
     const int nch = (int)min((int64_t)kChF, p.C - c0);
-    for (int e = threadIdx.x; e < kChF * n1; e += blockDim.x) {
-        const int ch = e / n1, j = e % n1;  // j fastest: coalesced reads of each channel's row
+    const int per_ch = blockDim.x / kChF;  // threads per channel
+    for (int ch = threadIdx.x / per_ch, j = threadIdx.x % per_ch; j < n1; j += per_ch) {
+        // consecutive threads read consecutive knots of one channel
         float xv, vv;
         if (ch < nch) {
             xv = p.knots[(c0 + ch) * (int64_t)n1 + j];
@@ -274,23 +283,30 @@ __device__ void build_tile_fwd(const ChanArgs& p, int64_t c0, float4* R, float* 
             atomicOr(&tp->any_chain, 1);
         }
     }
-    for (int e = threadIdx.x; e < K * kChF; e += blockDim.x) {
-        const int c = e / kChF, ch = e % kChF;
-        const int lb = lower_bound_cells8(cj + ch, n1, c);
-        float4 rec;
-        if (lb <= N && cj[lb * kChF + ch] == c) {  // knot lb is the cell's first knot
-            const int k = lb;
-            const bool chain = k < N && cj[(k + 1) * kChF + ch] == c;
-            const float sl = sp[max(k - 1, 0) * kChF + ch];
-            const float sr = chain ? make_knot_tag(k, true) : sp[k * kChF + ch];
-            rec = make_float4(xs[k * kChF + ch], vs[k * kChF + ch], sl, sr);
-        } else {  // inside interval lb: the line through (x_j, v_j), j = lb - 1, at the anchor
-            const int j = lb - 1;
-            const float sj = sp[j * kChF + ch];
-            const float xc = __fmaf_rn(__int2float_rn(c), tp->w[ch], tp->a[ch]);
-            rec = make_float4(xc, __fmaf_rn(__fsub_rn(xc, xs[j * kChF + ch]), sj, vs[j * kChF + ch]), sj, sj);
+    // cell records: each thread takes a run of consecutive cells of one
+    // channel, finds the first one's knot by bisection and walks on
+    {
+        const int ch = threadIdx.x % kChF, runs = blockDim.x / kChF, q = threadIdx.x / kChF;
+        const int per = (K + runs - 1) / runs;
+        const int cb = q * per, ce = min(K, cb + per);
+        int lb = cb < ce ? lower_bound_cells8(cj + ch, n1, cb) : 0;
+        for (int c = cb; c < ce; ++c) {
+            while (lb < n1 && cj[lb * kChF + ch] < c) ++lb;  // lb: the first knot whose cell is >= c
+            float4 rec;
+            if (lb <= N && cj[lb * kChF + ch] == c) {  // knot lb is the cell's first knot
+                const int k = lb;
+                const bool chain = k < N && cj[(k + 1) * kChF + ch] == c;
+                const float sl = sp[max(k - 1, 0) * kChF + ch];
+                const float sr = chain ? make_knot_tag(k, true) : sp[k * kChF + ch];
+                rec = make_float4(xs[k * kChF + ch], vs[k * kChF + ch], sl, sr);
+            } else {  // inside interval lb: the line through (x_j, v_j), j = lb - 1, at the anchor
+                const int j = lb - 1;
+                const float sj = sp[j * kChF + ch];
+                const float xc = __fmaf_rn(__int2float_rn(c), tp->w[ch], tp->a[ch]);
+                rec = make_float4(xc, __fmaf_rn(__fsub_rn(xc, xs[j * kChF + ch]), sj, vs[j * kChF + ch]), sj, sj);
+            }
+            R[c * kChF + ch] = rec;
         }
-        R[e] = rec;
     }
     __syncthreads();
 }
