@@ -35,7 +35,7 @@ constexpr int kBwdUnroll = 2;
 //   A[N+1]    gy of queries clamped on the right -> g_v[N]
 //   B[0..N+1] sum gy delta on interval i (entries 0 and N+1 unused)
 struct BwdArgs {
-    const float4* rec;  // backward records {x_j, j, s_j, s_{j+1} | link}
+    const float4* rec;  // backward records {x_j, j, s_j, s_{j+1} | link} or {x_j, j | inside, 1/h_{j+1}, s_{j+1}}
     const TableHeader* hdr;
     const float* inv_h;
     const float* slope;
@@ -73,13 +73,17 @@ __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restr
             r = (j < p.n_smem) ? srec[j] : __ldg(p.rec + j);
         }
     }
-    const int j = __float_as_int(r.y);
+    const uint32_t jy = __float_as_uint(r.y);
+    const bool inside = (jy & kInsideFlag) != 0;  // knot-free cell: 1/h_{j+1} in r.z
+    const int j = (int)(jy & ~kInsideFlag);
     // left of x_j: interval j, measured from its right end; else interval
     // j + 1 (an interior query never reaches x_N, where j + 1 would be N + 1)
-    const bool lside = xc < r.x;
+    const bool lside = !inside && xc < r.x;
     const int i = lside ? j : j + 1;
     const float s = lside ? r.z : r.w;
-    const float tt = (lside ? (r.x - xc) : (xc - r.x)) * s_ih[i];
+    float ih = r.z;
+    if (!inside) ih = s_ih[i];  // knot cells only: the shared gather of 1/h_i
+    const float tt = (lside ? (r.x - xc) : (xc - r.x)) * ih;
     const float delta = lside ? 1.0f - tt : tt;
     const float one_minus = lside ? tt : 1.0f - tt;
     const bool interior = x > p.a && x < p.b;  // false for NaN

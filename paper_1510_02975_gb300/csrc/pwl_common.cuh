@@ -157,6 +157,10 @@ constexpr uint32_t kLinkTag = 0x7FC00000u;
 constexpr uint32_t kLinkMask = 0x003FFFFFu;
 constexpr uint32_t kKnotTagMask = 0x001FFFFFu;  // knot index in a forward knot-cell tag
 constexpr uint32_t kKnotTagChain = 0x00200000u; // more knots share the cell
+// A backward record of a knot-free cell (the cell lies inside interval j + 1,
+// right of knot j) sets bit 31 of its index field and carries 1/h_{j+1} in
+// place of s_j: {x_j, j | kInsideFlag, 1/h_{j+1}, s_{j+1}}.
+constexpr uint32_t kInsideFlag = 0x80000000u;
 
 __device__ __forceinline__ bool is_link(float w)
 {

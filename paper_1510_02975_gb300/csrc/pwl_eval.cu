@@ -358,12 +358,14 @@ __global__ void __launch_bounds__(1024) eval_tex_kernel(const TexArgs p, cudaTex
             const int j = link_index(r.w);
             r = (j < n_stage) ? srec[j] : __ldg(p.rec + j);
         }
-        const int j = __float_as_int(r.y);
+        const uint32_t jy = __float_as_uint(r.y);
+        const bool inside = (jy & kInsideFlag) != 0;  // knot-free cell: 1/h_{j+1} in r.z
+        const int j = (int)(jy & ~kInsideFlag);
         float u;  // texel coordinate i - 1 + delta + 1/2
-        if (xc < r.x) {
+        if (!inside && xc < r.x) {
             u = (float)j + 0.5f - (r.x - xc) * s_ih[j];
         } else if (j < p.N) {
-            u = (float)j + 0.5f + (xc - r.x) * s_ih[j + 1];
+            u = (float)j + 0.5f + (xc - r.x) * (inside ? r.z : s_ih[j + 1]);
         } else {
             u = (float)p.N + 0.5f;
         }

@@ -145,7 +145,8 @@ __device__ void knot_cells(int N, int K, float inv_w, float off, const float* __
 
 __global__ void __launch_bounds__(kBuildThreads) table_index_b_kernel(
     int N, int K, float inv_w, float off, const float* __restrict__ xk, const float* __restrict__ vk,
-    const float* __restrict__ slope, int* cj, int* cpos, float4* rec16, float4* rec_b, TableHeader* hdr)
+    const float* __restrict__ slope, const float* __restrict__ inv_h, int* cj, int* cpos, float4* rec16,
+    float4* rec_b, TableHeader* hdr)
 {
     __shared__ int s_warp[33];
     __shared__ int s_maxchain;
@@ -167,15 +168,19 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_b_kernel(
         const int lb = lower_bound_int(cj, N + 1, c);
         int j;
         bool chained = false;
-        if (lb <= N && cj[lb] == c) {
+        const bool knot_cell = lb <= N && cj[lb] == c;
+        if (knot_cell) {
             j = lb;
             chained = (j < N && cj[j + 1] == c);
         } else {
-            j = lb - 1;
+            j = lb - 1;  // cell 0 holds knot 0 and cell K-1 knot N, so 0 <= j < N here
         }
         const float w = chained ? make_link(K + cpos[j + 1]) : slope[j + 1];
         rec16[c] = make_float4(xk[j], vk[j], slope[j], w);
-        rec_b[c] = make_float4(xk[j], __int_as_float(j), slope[j], w);
+        // a knot-free cell's queries all lie in interval j + 1 (the cell
+        // function is monotone): its record carries that interval's 1/h
+        rec_b[c] = knot_cell ? make_float4(xk[j], __int_as_float(j), slope[j], w)
+                             : make_float4(xk[j], __uint_as_float(kInsideFlag | (uint32_t)j), inv_h[j + 1], w);
     }
     for (int j = 1 + threadIdx.x; j <= N; j += blockDim.x) {
         if (cj[j] != cj[j - 1]) continue;
@@ -244,7 +249,7 @@ pwl_status launch_build(pwl_table t, const double* d_knots, const double* d_valu
         PWL_CHECK_LAUNCH("table_round_kernel");
     }
     table_index_b_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->Kb, t->inv_w_b, t->off_b, t->xk, t->vk, t->slope,
-                                                     t->cj, t->cpos, t->rec16, t->rec_b, t->hdr);
+                                                     t->inv_h, t->cj, t->cpos, t->rec16, t->rec_b, t->hdr);
     PWL_CHECK_LAUNCH("table_index_b_kernel");
     table_index_f_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->K, t->inv_w, t->off, t->w, t->a, t->xk, t->vk,
                                                      t->slope, t->cj, t->recP, t->recS, t->hdr);
