@@ -450,8 +450,25 @@ def small_case(wl, reps: int = 50):
         t = pwl.Table(kn, pwl.pwl_project(f, kn, form))
         sec = time_launches(lambda: pwl.pwl_eval(t.handle, x, y), reps)
         err = float(np.abs(y.cpu().numpy().astype(np.float64) - f64("gaussian", xd)).max())
+        # the same launches replayed from a CUDA graph: device time per launch
+        # without the per-call host work (argument checks, ctypes, launch)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                pwl.pwl_eval(t.handle, x, y)
+        graph.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        gsec = e0.elapsed_time(e1) / reps / 1e3
         out[form] = {"us_per_launch": round(sec * 1e6, 2), "G_evals_per_s": round(sc["m"] / sec / 1e9, 1),
-                     "max_err_vs_f64_f": err}
+                     "us_per_launch_graph": round(gsec * 1e6, 2),
+                     "G_evals_per_s_graph": round(sc["m"] / gsec / 1e9, 1), "max_err_vs_f64_f": err}
+        del graph
         t.close()
     return out
 
@@ -813,7 +830,7 @@ def run_batched(args):
     ev_gbs = BYTES_FWD * nq / phases["eval"] / 1e9
     out = {
         "report": "batched", "n_funcs": len(funcs), "total_knots": int(info["total_knots"]),
-        "total_queries": nq, "m_per_interval": args.batch_m, "cells_per_knot": args.batch_cpk or 4,
+        "total_queries": nq, "m_per_interval": args.batch_m, "cells_per_knot": args.batch_cpk or 3,
         "step_ms": round(step * 1e3, 4),
         "step_G_evals_per_s": round(nq / step / 1e9, 2),
         "phase_ms": {k: round(v * 1e3, 4) for k, v in phases.items()},

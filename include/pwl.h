@@ -260,7 +260,7 @@ pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, f
  *   m_per_interval density cells per interval of the design step
  *                  (M_f = m_per_interval N_f); 0 selects 64
  *   cells_per_knot cells of each function's evaluation index per knot
- *                  (0 selects 4), reduced where the index would not fit one
+ *                  (0 selects 3), reduced where the index would not fit one
  *                  CTA's shared memory
  * Allocates all device memory of the batch (synchronously); the batch owns
  * it until pwl_batch_destroy.  Errors: PWL_EINVAL (sizes, a descriptor),

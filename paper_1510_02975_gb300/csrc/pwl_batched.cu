@@ -625,7 +625,7 @@ pwl_status pwl_batch_create(const pwl_func* funcs, const int64_t* n_intervals, i
     if (m_per_interval < 0 || m_per_interval > 4096) return fail(PWL_EINVAL, "m_per_interval must be in [0, 4096]");
     if (cells_per_knot < 0 || cells_per_knot > 64) return fail(PWL_EINVAL, "cells_per_knot must be in [0, 64]");
     const int64_t mper = m_per_interval > 0 ? m_per_interval : 64;
-    const int64_t cpk = cells_per_knot > 0 ? cells_per_knot : 4;
+    const int64_t cpk = cells_per_knot > 0 ? cells_per_knot : 3;
     for (int64_t f = 0; f < n_funcs; ++f) {
         if (validate_func(funcs + f) != PWL_OK) return fail(PWL_EINVAL, "function %lld: %s", (long long)f,
                                                             pwl_last_error());
@@ -900,7 +900,7 @@ pwl_status pwl_batch_eval(pwl_batch b, const float* d_x, float* d_y, void* strea
     if ((reinterpret_cast<uintptr_t>(d_x) | reinterpret_cast<uintptr_t>(d_y)) % 16 != 0)
         return fail(PWL_EINVAL, "x and y must be 16-byte aligned");
     const EvalShape& sh = kShapes[b->shape];
-    PWL_CUDA_TRY(cudaFuncSetAttribute(sh.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    PWL_CUDA_TRY(raise_smem_limit(sh.kern, b->smem));
     const EvalParams p{b->items, b->range, b->n_ranges, b->counter, b->bf, b->xk, b->recP, b->recS,
                        b->buf_stride, b->status};
     if (sh.stage != kStageAsync)

@@ -4,7 +4,11 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <deque>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "pwl_common.cuh"
@@ -33,7 +37,7 @@ pwl_status cuda_fail(cudaError_t e, const char* what)
 const DeviceInfo& device_info()
 {
     static std::mutex mu;
-    static std::vector<DeviceInfo> cache;
+    static std::deque<DeviceInfo> cache;  // references stay valid as devices are added
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
@@ -52,6 +56,52 @@ const DeviceInfo& device_info()
     d.max_threads_sm = v > 0 ? v : 2048;
     cache.push_back(d);
     return cache.back();
+}
+
+// The dynamic shared-memory limit is a per-function maximum: it is raised
+// when a launch needs more and never lowered, so a cached grid stays valid.
+// Both it and the occupancy query are host calls that cost more than a small
+// launch, hence the caches (per device and kernel).
+namespace {
+std::mutex g_launch_mu;
+std::map<std::pair<int, const void*>, size_t> g_smem_limit;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_grid;
+
+cudaError_t ensure_smem_limit_locked(int dev, const void* fn, size_t smem)
+{
+    size_t& lim = g_smem_limit[std::make_pair(dev, fn)];
+    if (lim >= smem && lim != 0) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) lim = std::max(lim, smem);
+    return e;
+}
+}  // namespace
+
+cudaError_t ensure_smem_limit(const void* fn, size_t smem)
+{
+    const int dev = device_info().device;
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    return ensure_smem_limit_locked(dev, fn, smem);
+}
+
+cudaError_t occupancy_grid_fn(const void* fn, int threads, size_t smem, int* grid)
+{
+    const DeviceInfo& di = device_info();
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    cudaError_t e = ensure_smem_limit_locked(di.device, fn, smem);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple(di.device, fn, threads, smem);
+    const auto it = g_grid.find(key);
+    if (it != g_grid.end()) {
+        *grid = it->second;
+        return cudaSuccess;
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    *grid = std::max(occ, 1) * di.sms;
+    g_grid[key] = *grid;
+    return cudaSuccess;
 }
 
 pwl_status validate_func(const pwl_func* f)

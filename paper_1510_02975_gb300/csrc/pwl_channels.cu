@@ -629,7 +629,7 @@ pwl_status channels_launch(const ChanArgs& base, bool backward, int io_dtype, co
         kfn = (const void*)channels_forward_kernel<__nv_bfloat16>;
     else
         kfn = (const void*)channels_forward_kernel<float>;
-    PWL_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PWL_CUDA_TRY(ensure_smem_limit(kfn, smem));
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

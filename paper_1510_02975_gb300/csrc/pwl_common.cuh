@@ -40,6 +40,16 @@ struct DeviceInfo {
 };
 // properties of the current device (cached per device)
 const DeviceInfo& device_info();
+// Raises a kernel's dynamic shared-memory limit to at least smem (never
+// lowers it), and the persistent grid of a kernel (resident CTAs per SM
+// times the SM count) with that limit set; both cached per device and kernel.
+cudaError_t ensure_smem_limit(const void* fn, size_t smem);
+cudaError_t occupancy_grid_fn(const void* fn, int threads, size_t smem, int* grid);
+template <typename Kern>
+inline cudaError_t raise_smem_limit(Kern kern, size_t smem)
+{
+    return ensure_smem_limit(reinterpret_cast<const void*>(kern), smem);
+}
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -434,11 +434,14 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
         kern = two ? eval_kernel<IO, 1, 2> : eval_kernel<IO, 1, 1>;
     int max_grid = 0;
     PWL_CUDA_TRY(occupancy_grid(kern, 1024, smem, &max_grid));
-    // no more CTAs than there are unrolled vector groups (small launches
-    // should not stage the index in hundreds of idle CTAs)
+    // small launches: no more CTAs than there are unrolled vector groups,
+    // but one per SM while each gets a few vectors per warp (the CTAs stage
+    // the index concurrently, so spreading costs no latency and uses every
+    // SM's loads); tiny ones do not stage the index in idle CTAs
     const int64_t units = p.nvec + (m - p.nvec * Vec<IO>::n);
     const int64_t per_cta = (int64_t)1024 * kUnroll;
-    const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, (units + per_cta - 1) / per_cta));
+    const int64_t spread = std::min<int64_t>(device_info().sms, (units + 255) / 256);
+    const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(spread, (units + per_cta - 1) / per_cta));
     kern<<<grid, 1024, smem, s>>>(p, x, y, m);
     PWL_CHECK_LAUNCH("eval_kernel");
     return PWL_OK;

@@ -417,8 +417,7 @@ pwl_status project_launch(const ProjectPlan& p, const GaussLegendre& gl, cudaStr
     const size_t smem = sizeof(double) * 4 * (size_t)p.max_rows;
     const int use_smem = smem <= di.smem_optin ? 1 : 0;
     if (use_smem) {
-        PWL_CUDA_TRY(cudaFuncSetAttribute(gram_solve_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PWL_CUDA_TRY(raise_smem_limit(gram_solve_kernel, smem));
     }
     gram_solve_kernel<<<(int)std::min<int64_t>(p.F, 65535), kSolveThreads, use_smem ? smem : 0, s>>>(
         p, use_smem);

@@ -66,18 +66,12 @@ inline size_t backward_smem_bytes(const pwl_table_s* t)
 }
 
 // Persistent grid of a kernel: resident CTAs per SM (registers, shared
-// memory, threads) times the SM count.  Sets the kernel's dynamic shared
-// memory limit first, which the occupancy query takes into account.
+// memory, threads) times the SM count, with the kernel's dynamic shared
+// memory limit raised to smem first (cached host calls).
 template <typename Kern>
 inline cudaError_t occupancy_grid(Kern kern, int threads, size_t smem, int* grid)
 {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-    if (e != cudaSuccess) return e;
-    *grid = std::max(occ, 1) * device_info().sms;
-    return cudaSuccess;
+    return occupancy_grid_fn(reinterpret_cast<const void*>(kern), threads, smem, grid);
 }
 
 }  // namespace pwl
