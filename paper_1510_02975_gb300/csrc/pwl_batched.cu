@@ -184,12 +184,14 @@ __device__ __forceinline__ void batch_range(const Lookup& d, const float2* P, co
                                             int64_t q1)
 {
     // 16-byte vectors between the first and the last 16-byte boundary of the
-    // range, scalar head and tail
+    // range, scalar head and tail (fewer than 4 queries each).  The head and
+    // tail loads go out first and complete while the vectors stream.
     const int64_t v0 = min(q1, (q0 + 3) & ~(int64_t)3);
     const int64_t v1 = max(v0, q1 & ~(int64_t)3);
     const int nt = blockDim.x;
-    for (int j = threadIdx.x; j < (int)(v0 - q0); j += nt)
-        y[q0 + j] = batch_lerp<CHAINS, STAGED>(x[q0 + j], d, P, S, xk);
+    const bool has_h = threadIdx.x < (int)(v0 - q0), has_t = threadIdx.x < (int)(q1 - v1);
+    const float xh = has_h ? x[q0 + threadIdx.x] : 0.0f;
+    const float xt = has_t ? x[v1 + threadIdx.x] : 0.0f;
     const float4* xv = reinterpret_cast<const float4*>(x + v0);
     float4* yv = reinterpret_cast<float4*>(y + v0);
     const int nv = (int)((v1 - v0) / 4);
@@ -216,8 +218,8 @@ __device__ __forceinline__ void batch_range(const Lookup& d, const float2* P, co
         a.w = batch_lerp<CHAINS, STAGED>(a.w, d, P, S, xk);
         __stcs(yv + i, a);
     }
-    for (int j = threadIdx.x; j < (int)(q1 - v1); j += nt)
-        y[v1 + j] = batch_lerp<CHAINS, STAGED>(x[v1 + j], d, P, S, xk);
+    if (has_h) y[q0 + threadIdx.x] = batch_lerp<CHAINS, STAGED>(xh, d, P, S, xk);
+    if (has_t) y[v1 + threadIdx.x] = batch_lerp<CHAINS, STAGED>(xt, d, P, S, xk);
 }
 
 // Queries q0 .. q1-1 of one function, the 16-byte vectors streamed through a

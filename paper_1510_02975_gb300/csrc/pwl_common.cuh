@@ -193,6 +193,19 @@ __device__ __forceinline__ int cell_of(float xc, float inv_w, float off, int K)
     return min(max(c, 0), K - 1);
 }
 
+// cell_of, and the cell number as a float, without float <-> int
+// conversions: for 0 <= t < 2^23, t + 2^23 rounded toward -inf is
+// 2^23 + floor(t) (the spacing of floats in [2^23, 2^24) is 1), so floor(t)
+// is the float (t + 2^23) - 2^23 and, as an integer, the low mantissa bits
+// of its sum with 2^23.  Clamped like cell_of, it returns the same cell for
+// every finite t and for NaN (cell 0); needs K <= 2^22.
+__device__ __forceinline__ int cell_of_f(float xc, float inv_w, float off, int K, float& cf)
+{
+    const float t = __fmaf_rn(xc, inv_w, off);
+    cf = fminf(fmaxf(__fsub_rn(__fadd_rd(t, 0x1p23f), 0x1p23f), 0.0f), (float)(K - 1));
+    return __float_as_int(__fadd_rn(cf, 0x1p23f)) - 0x4B000000;
+}
+
 // clamp to [a, b] with NaN propagation
 __device__ __forceinline__ float clamp_nan(float x, float a, float b)
 {

@@ -59,10 +59,11 @@ struct Lerp8 {
     __device__ __forceinline__ float operator()(float x) const
     {
         const float xc = clamp_nan(x, p.a, p.b);
-        const int c = cell_of(xc, p.inv_w, p.off, p.K);
+        float cf;
+        const int c = cell_of_f(xc, p.inv_w, p.off, p.K, cf);
         const float2 r = sP[c];
         const uint32_t bits = __float_as_uint(r.x);
-        float anchor = __fmaf_rn(__int2float_rn(c), p.w, p.a);
+        float anchor = __fmaf_rn(cf, p.w, p.a);
         float2 q = r;  // no knot in the cell: the cell's line {y_c, s} anchored at x_c
         if ((bits & 0xFFC00000u) == kLinkTag) {
             int k = (int)(bits & kKnotTagMask);
