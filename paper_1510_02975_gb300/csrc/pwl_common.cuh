@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "pwl.h"
+#include "pwl_bessel.cuh"
 
 namespace pwl {
 
@@ -61,15 +62,15 @@ struct FMath;
 template <>
 struct FMath<double> {
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
-    static __device__ __forceinline__ double bj0(double x) { return j0(x); }
-    static __device__ __forceinline__ double bj1(double x) { return j1(x); }
+    static __device__ __forceinline__ double bj0(double x) { return bessel_j0(x); }
+    static __device__ __forceinline__ double bj1(double x) { return bessel_j1(x); }
     static __device__ __forceinline__ double pw(double x, double y) { return pow(x, y); }
 };
 template <>
 struct FMath<float> {
     static __device__ __forceinline__ float ex(float x) { return expf(x); }
-    static __device__ __forceinline__ float bj0(float x) { return j0f(x); }
-    static __device__ __forceinline__ float bj1(float x) { return j1f(x); }
+    static __device__ __forceinline__ float bj0(float x) { return bessel_j0(x); }
+    static __device__ __forceinline__ float bj1(float x) { return bessel_j1(x); }
     static __device__ __forceinline__ float pw(float x, float y) { return powf(x, y); }
 };
 

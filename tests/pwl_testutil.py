@@ -9,6 +9,11 @@ Tolerances (from the arithmetic):
     1e-12 max|v| (different summation orders and cyclic reduction vs Thomas).
   Table gradients (FP32 accumulation): within 1e-5 of the sum of the
     absolute values of the accumulated terms (FP64 reference).
+  FP32 design mode (FP32 densities, compensated sums, FP64 scan and
+    inversion): a relative density error eps moves knot i by about
+    eps N (G(x_i) / G_M) h_i, so each knot is held within
+    max(1e-3, 1e-6 N) of the shorter of its two intervals (eps up to ~1e-6:
+    the FP32 f'' of J0 near its zeros).
 """
 import numpy as np
 
@@ -16,6 +21,13 @@ EVAL_REL = 5e-7
 DESIGN_REL = 1e-12
 VALUES_REL = 1e-12
 GRAD_REL = 1e-5
+
+
+def fp32_design_bound(ref_knots) -> np.ndarray:
+    """Per-knot bound of the FP32 design mode against the FP64 oracle."""
+    h = np.diff(ref_knots)
+    h_adj = np.minimum(np.r_[h[0], h], np.r_[h, h[-1]])
+    return max(1e-3, 1e-6 * h.size) * h_adj
 
 
 def round_values(v, dtype: str) -> np.ndarray:

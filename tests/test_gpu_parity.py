@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from pwl_testutil import DESIGN_REL, EVAL_REL, GRAD_REL, VALUES_REL, round_knots, round_values
+from pwl_testutil import DESIGN_REL, EVAL_REL, GRAD_REL, VALUES_REL, fp32_design_bound, round_knots, round_values
 
 pytestmark = pytest.mark.gpu
 
@@ -55,15 +55,15 @@ def test_design_linear_function_is_uniform(pwl):
     assert np.allclose(got, -1.0 + np.arange(13) * 0.25, atol=1e-15)
 
 
-def test_design_fp32_density_mode(pwl, workloads):
-    # FP32 integrand: knots move by about (FP32 rounding of d) / d * h
+@pytest.mark.parametrize("N", [1024, 4096])
+def test_design_fp32_density_mode(pwl, workloads, N):
+    # FP32 integrand: a relative density error eps moves knot i by about
+    # eps N (G(x_i) / G_M) h_i (fp32_design_bound)
     for name in FUNCS:
         f = workloads.PAPER_FUNCTIONS[name]
-        N = 1024
         got = pwl.pwl_design(f, N, 0, "fp32").cpu().numpy()
         ref = oracle.design(f, N)
-        h = np.diff(ref).min()
-        assert np.abs(got - ref).max() <= 1e-3 * h
+        assert np.all(np.abs(got - ref) <= fp32_design_bound(ref)), name
 
 
 @pytest.mark.parametrize("name", FUNCS)
