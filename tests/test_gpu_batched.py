@@ -200,6 +200,26 @@ def test_batch_fp32_density_design(pwl, workloads):
     b.close()
 
 
+def test_batch_fp64_bessel_large_arguments(pwl):
+    # J0(alpha x) on [0, 50] with alpha up to 5: z = alpha x up to 250, where
+    # the FP64 J0/J1 must stay near 1e-16 for the knots to meet DESIGN_REL
+    funcs = [{"kind": "bessel_j0", "a": 0.0, "b": 50.0, "p": [1.0, al]} for al in (3.0, 4.2, 5.0, 0.7)]
+    n_int = [2500, 4000, 3100, 4095]
+    b = pwl.Batch(funcs, n_int, m_per_interval=16)
+    b.design("fp64")
+    b.project("project")
+    knots = b.knots().cpu().numpy()
+    vals = b.values().cpu().numpy()
+    off = b.offsets()
+    for i, f in enumerate(funcs):
+        kn = knots[off[i]:off[i + 1]]
+        ref = oracle.design(f, n_int[i], 16 * n_int[i])
+        assert np.abs(kn - ref).max() <= DESIGN_REL * (f["b"] - f["a"]), i
+        vref = oracle.values(f, kn, "project")
+        assert np.abs(vals[off[i]:off[i + 1]] - vref).max() <= VALUES_REL * np.abs(vref).max(), i
+    b.close()
+
+
 def test_batch_design_degenerate_densities(pwl):
     # f linear (f'' = 0): G_M = 0 and the uniform partition, as the oracle;
     # a Gaussian on [-30, 30] in FP32 mode: the FP32 density underflows to 0
