@@ -10,15 +10,13 @@ Q_nu = sqrt(pi x / 2) (Y_nu cos chi - J_nu sin chi).  Both are smooth in
 u = (8 / x)^2 on (0, 1] (P_nu -> 1, Q_nu ~ (4 nu^2 - 1) / (8 x)).  This
 script evaluates P_nu and (x / 8) Q_nu with mpmath at 45 digits at the n
 Chebyshev nodes of w = 2 u - 1 and prints the Chebyshev interpolation
-coefficients (the truncated series is accurate to ~1e-19 at n = 16), and
-the first 6 of them rounded to FP32 for the FP32 evaluation.
+coefficients (the truncated series is accurate to ~1e-19 at n = 16).
 
 Run: python gen_bessel_pq.py > pwl_bessel_tables.cuh   (needs mpmath)
 """
 import mpmath as mp
 
 N_COEF = 16
-N_COEF_F = 6
 
 
 def pq(nu, x):
@@ -54,10 +52,6 @@ def main():
     for (nu, which), c in coef.items():
         body = ",\n    ".join(mp.nstr(v, 20, min_fixed=1, max_fixed=0) for v in c)
         print("static __device__ __constant__ double kBessel%s%d[%d] = {\n    %s};" % (which, nu, N_COEF, body))
-    # FP32: the first N_COEF_F coefficients (the rest are below 1e-12)
-    for (nu, which), c in coef.items():
-        body = ", ".join(mp.nstr(v, 10, min_fixed=1, max_fixed=0) + "f" for v in c[:N_COEF_F])
-        print("static __device__ __constant__ float kBessel%s%df[%d] = {%s};" % (which, nu, N_COEF_F, body))
     print("}  // namespace pwl")
 
 

@@ -12,8 +12,7 @@
 // w = 2 (8/x)^2 - 1 (pwl_bessel_tables.cuh, from gen_bessel_pq.py), and with
 //     cos chi0 = (cos x + sin x) / sqrt 2,   sin chi0 = (sin x - cos x) / sqrt 2,
 //     cos chi1 = (sin x - cos x) / sqrt 2,   sin chi1 = -(sin x + cos x) / sqrt 2:
-// absolute error ~3e-16 in FP64, and a few FP32 ulps of sqrt(2 / (pi x)) in
-// FP32 (the series cut to 6 terms).
+// absolute error ~3e-16.
 #pragma once
 
 #include <math.h>
@@ -45,7 +44,7 @@ __device__ __forceinline__ double bessel_j0(double x)
     const double q = t * chebyshev_sum<double, 16>(kBesselQ0, w);
     double s, c;
     sincos(ax, &s, &c);
-    return (p * (c + s) - q * (s - c)) / sqrt(3.14159265358979323846 * ax);
+    return (p * (c + s) - q * (s - c)) * rsqrt(3.14159265358979323846 * ax);
 }
 
 __device__ __forceinline__ double bessel_j1(double x)
@@ -57,33 +56,40 @@ __device__ __forceinline__ double bessel_j1(double x)
     const double q = t * chebyshev_sum<double, 16>(kBesselQ1, w);
     double s, c;
     sincos(ax, &s, &c);
-    const double r = (p * (s - c) + q * (s + c)) / sqrt(3.14159265358979323846 * ax);
+    const double r = (p * (s - c) + q * (s + c)) * rsqrt(3.14159265358979323846 * ax);
     return x < 0.0 ? -r : r;
 }
 
-__device__ __forceinline__ float bessel_j0(float x)
+// FP32 (the FP32 design mode): the library's j0f / j1f (absolute error
+// ~5e-7), within the FP32 mode's knot bound.
+__device__ __forceinline__ float bessel_j0(float x) { return j0f(x); }
+__device__ __forceinline__ float bessel_j1(float x) { return j1f(x); }
+
+// J0 and J1 at the same point (f'' needs both): one sincos and one square
+// root for the two.
+__device__ __forceinline__ void bessel_j01(double x, double& j0v, double& j1v)
 {
-    const float ax = fabsf(x);
-    if (ax < 8.0f) return j0f(x);
-    const float t = 8.0f / ax, w = 2.0f * t * t - 1.0f;
-    const float p = chebyshev_sum<float, 6>(kBesselP0f, w);
-    const float q = t * chebyshev_sum<float, 6>(kBesselQ0f, w);
-    float s, c;
-    sincosf(ax, &s, &c);
-    return (p * (c + s) - q * (s - c)) / sqrtf(3.14159265f * ax);
+    const double ax = fabs(x);
+    if (ax < 8.0) {
+        j0v = j0(x);
+        j1v = j1(x);
+        return;
+    }
+    const double t = 8.0 / ax, w = 2.0 * t * t - 1.0;
+    const double p0 = chebyshev_sum<double, 16>(kBesselP0, w), q0 = t * chebyshev_sum<double, 16>(kBesselQ0, w);
+    const double p1 = chebyshev_sum<double, 16>(kBesselP1, w), q1 = t * chebyshev_sum<double, 16>(kBesselQ1, w);
+    double s, c;
+    sincos(ax, &s, &c);
+    const double r = rsqrt(3.14159265358979323846 * ax);
+    j0v = (p0 * (c + s) - q0 * (s - c)) * r;
+    const double j1a = (p1 * (s - c) + q1 * (s + c)) * r;
+    j1v = x < 0.0 ? -j1a : j1a;
 }
 
-__device__ __forceinline__ float bessel_j1(float x)
+__device__ __forceinline__ void bessel_j01(float x, float& j0v, float& j1v)
 {
-    const float ax = fabsf(x);
-    if (ax < 8.0f) return j1f(x);
-    const float t = 8.0f / ax, w = 2.0f * t * t - 1.0f;
-    const float p = chebyshev_sum<float, 6>(kBesselP1f, w);
-    const float q = t * chebyshev_sum<float, 6>(kBesselQ1f, w);
-    float s, c;
-    sincosf(ax, &s, &c);
-    const float r = (p * (s - c) + q * (s + c)) / sqrtf(3.14159265f * ax);
-    return x < 0.0f ? -r : r;
+    j0v = j0f(x);
+    j1v = j1f(x);
 }
 
 }  // namespace pwl

@@ -123,8 +123,10 @@ __device__ __forceinline__ T func_second_derivative(const pwl_func& F, T x)
     case PWL_F_BESSEL_J0: {
         T al = (T)F.p[1];
         T z = al * x;
-        T r = (fabs(z) < T(1e-8)) ? T(0.5) - z * z / T(16) : M::bj1(z) / z;
-        return (T)F.p[0] * al * al * (r - M::bj0(z));
+        T b0, b1;
+        bessel_j01(z, b0, b1);
+        T r = (fabs(z) < T(1e-8)) ? T(0.5) - z * z / T(16) : b1 / z;
+        return (T)F.p[0] * al * al * (r - b0);
     }
     case PWL_F_POLY: {
         T s = T(0);
@@ -135,6 +137,74 @@ __device__ __forceinline__ T func_second_derivative(const pwl_func& F, T x)
         return (T)F.p[0] * (T)F.p[1] * (T)F.p[1] * M::ex((T)F.p[1] * x);
     }
     return T(0);
+}
+
+// FP32 evaluation of f'' (the FP32 design mode) from constants converted
+// once per function: a double -> float conversion (or an FP32 division) per
+// evaluation would put an operation on the FP64 pipe or several
+// instructions in front of every density sample.  Kind-specific constants
+// (each formed in FP64, then rounded): Gaussian and Lorentzian
+// c = {A, mu, 1/s, A/s^2}; J0(alpha x) c = {A, alpha, -, A alpha^2};
+// exponential c = {A, lambda, -, A lambda^2}; polynomial d = the
+// coefficients of f'' (k (k-1) p_k at degree k - 2).
+struct FuncF {
+    int kind;
+    float c[4];
+    float d[6];
+};
+
+__device__ __forceinline__ FuncF make_funcf(const pwl_func& F)
+{
+    FuncF g{};
+    g.kind = F.kind;
+    switch (F.kind) {
+    case PWL_F_GAUSSIAN:
+    case PWL_F_LORENTZIAN:
+        g.c[0] = (float)F.p[0];
+        g.c[1] = (float)F.p[1];
+        g.c[2] = (float)(1.0 / F.p[2]);
+        g.c[3] = (float)(F.p[0] / (F.p[2] * F.p[2]));
+        break;
+    case PWL_F_BESSEL_J0:
+    case PWL_F_EXP:
+        g.c[0] = (float)F.p[0];
+        g.c[1] = (float)F.p[1];
+        g.c[3] = (float)(F.p[0] * F.p[1] * F.p[1]);
+        break;
+    default:  // PWL_F_POLY
+        for (int k = 2; k < 8; ++k) g.d[k - 2] = (float)((double)(k * (k - 1)) * F.p[k]);
+        break;
+    }
+    return g;
+}
+
+__device__ __forceinline__ float func_second_derivative_f(const FuncF& g, float x)
+{
+    switch (g.kind) {
+    case PWL_F_GAUSSIAN: {
+        const float u = (x - g.c[1]) * g.c[2];
+        return g.c[3] * (u * u - 1.0f) * expf(-0.5f * u * u);
+    }
+    case PWL_F_LORENTZIAN: {
+        const float u = (x - g.c[1]) * g.c[2];
+        const float q = 1.0f + u * u;
+        return g.c[3] * (6.0f * u * u - 2.0f) / (q * q * q);
+    }
+    case PWL_F_BESSEL_J0: {
+        const float z = g.c[1] * x;
+        float b0, b1;
+        bessel_j01(z, b0, b1);
+        const float r = (fabsf(z) < 1e-4f) ? 0.5f - z * z * 0.0625f : b1 / z;
+        return g.c[3] * (r - b0);
+    }
+    case PWL_F_EXP:
+        return g.c[3] * expf(g.c[1] * x);
+    default: {
+        float s = 0.0f;
+        for (int k = 5; k >= 0; --k) s = s * x + g.d[k];
+        return s;
+    }
+    }
 }
 
 // host-side descriptor validation

@@ -257,15 +257,14 @@ __device__ __forceinline__ double fused_density<double>(const pwl_func& F, doubl
     const double t = __dadd_rn(a, __dmul_rn((double)k + 0.5, delta));
     return pow(fabs(func_second_derivative<double>(F, t)), 0.4);
 }
-template <>
-__device__ __forceinline__ float fused_density<float>(const pwl_func& F, double, double, int64_t, float t0f,
-                                                      float deltaf, int local)
+// FP32 density from the function's FP32 constants: |f''|^{2/5} by the
+// hardware exp2/log2 pair (__powf), a few ulp (the FP32 mode's knot bound
+// allows a relative density error near 1e-6), for a third of the
+// instructions of powf
+__device__ __forceinline__ float fused_density_f(const FuncF& G, float t0f, float deltaf, int local)
 {
     const float t = __fmaf_rn((float)local + 0.5f, deltaf, t0f);
-    // |f''|^{2/5} by the hardware exp2/log2 pair (__powf): a few ulp, far
-    // below what the FP32 density mode promises (knots within 1e-3 of the
-    // shortest interval), for a third of the instructions of powf
-    return __powf(fabsf(func_second_derivative<float>(F, t)), 0.4f);
+    return __powf(fabsf(func_second_derivative_f(G, t)), 0.4f);
 }
 
 // smallest i in [1, N] with tau_i = i G_M / N >= G (N if none below N)
@@ -551,6 +550,7 @@ __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(De
     for (int o = blockIdx.x; o < p.F; o += gridDim.x) {
         const int f = p.order[o];
         const pwl_func F = p.funcs[f];
+        const FuncF G = make_funcf(F);  // FP32 constants of f'', once per function
         const int64_t M = p.moff[f + 1] - p.moff[f];
         const int64_t N = p.koff[f + 1] - p.koff[f] - 1;
         const int64_t nch = p.choff[f + 1] - p.choff[f];
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(De
             for (int r = 0; r < kPerThread; ++r) {
                 const int l = t * kPerThread + r;
                 if (l < cnt) {
-                    const float dk = fused_density<float>(F, a, delta, c0 + l, t0f, deltaf, l);
+                    const float dk = fused_density_f(G, t0f, deltaf, l);
                     dbuf[c0 + l] = dk;
                     part = ff_add(part, FF{dk, 0.0f});
                     if (dk > 0.0f) last = l;
