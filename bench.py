@@ -103,6 +103,14 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def replica_throughput(dist, ms: float, evals_per_step: int, steps: int):
+    """Whole-job throughput of independent replicas (weak scaling): every rank
+    ran evals_per_step x steps evaluations and the job took the slowest rank's
+    time.  Returns (G evals/s over all ranks, that time in ms)."""
+    ms_max = dist.max(ms)
+    return dist.world * evals_per_step * steps / (ms_max / 1e3) / 1e9, ms_max
+
+
 # ----------------------------------------------------------------------------
 # clocks during the timed region
 # ----------------------------------------------------------------------------
@@ -338,11 +346,9 @@ def run_ours(args):
     dist.barrier()
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
-    ms_max = dist.max(ms)
+    value, ms_max = replica_throughput(dist, ms, wl.evals_per_step, args.steps)
     launch_ms = [a.elapsed_time(b) for a, b in events]
     avg_launch_s = float(np.mean(launch_ms)) / 1e3
-    total_evals = wl.evals_per_step * args.steps * dist.world
-    value = total_evals / (ms_max / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     achieved = BYTES_FWD * wl.m / avg_launch_s / 1e9
 
