@@ -671,7 +671,9 @@ def run_variants(args):
     """Per-table throughput of the evaluation paths (main cell-index path, the
     paper's binary search, the texture filter) for the three functions and
     N in {256, 1024, 4096}, and, at N = 1024, the error of FP32 / BF16 / FP16
-    vertex tables (max and RMS vs FP64 f and vs the FP64 CPWL)."""
+    vertex tables (max and RMS vs FP64 f and vs the FP64 CPWL); then the N
+    each function needs for a target L2 error on the nearly optimal and on
+    the uniform partition (Results 4-6)."""
     import torch
 
     import paper_1510_02975_gb300 as pwl
@@ -720,9 +722,21 @@ def run_variants(args):
                                        "max_vs_f64_pwl": float(np.abs(ep).max()),
                                        "rms_vs_f64_pwl": float(np.sqrt(np.mean(ep * ep)))})
                 t.close()
+    # N for a target L2 error on the nearly optimal and on the uniform
+    # partition (Results 4-6): the memory the optimised partition saves
+    sizing = []
+    for name in FUNC_NAMES:
+        f = W.PAPER_FUNCTIONS[name]
+        i25, isq = (float(v) for v in pwl.pwl_error_constants(f).cpu())
+        for target in (1e-4, 1e-6, 1e-8):
+            for form in ("interp", "project"):
+                n_opt = pwl.pwl_n_for_error(i25, isq, f["a"], f["b"], target, form, False)
+                n_uni = pwl.pwl_n_for_error(i25, isq, f["a"], f["b"], target, form, True)
+                sizing.append({"func": name, "target_l2": target, "form": form, "N_optimised": n_opt,
+                               "N_uniform": n_uni, "uniform_over_optimised": round(n_uni / n_opt, 3)})
     peak, kind = measured_peaks()
     print(json.dumps({"report": "variants", "queries_per_launch": m, "peak_gbs": peak, "peak_kind": kind,
-                      "throughput": rows, "errors": errors}), flush=True)
+                      "throughput": rows, "errors": errors, "n_for_error": sizing}), flush=True)
 
 
 def run_channels(args):

@@ -143,6 +143,41 @@ pwl_status pwl_project(const pwl_func* f, const double* d_knots, int64_t n_inter
                        void* d_workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* A priori errors and the N for a target error (Results 4-6, Section III-B) */
+/* ------------------------------------------------------------------------ */
+
+/* The two integrals the error results need, by the midpoint rule on m_cells
+ * uniform cells t_k = a + (k + 1/2)(b - a)/M (the discretisation of
+ * pwl_design) in FP64:
+ *   d_out[0] = integral over [a, b] of |f''|^{2/5}   (Result 4)
+ *   d_out[1] = integral over [a, b] of f''^2         (Result 6, ||f''||^2)
+ *   f        host pointer to the function descriptor
+ *   m_cells  M >= 1; 0 selects 2^20
+ *   d_out    device, 2 doubles (overwritten)
+ * Asynchronous on stream.  Errors: PWL_EINVAL (descriptor, sizes, NULL).    */
+pwl_status pwl_error_constants(const pwl_func* f, int64_t m_cells, double* d_out, void* stream);
+
+/* Predicted L2 error of the CPWL approximation with N intervals (host only):
+ *   form PWL_INTERP, uniform = 0 (T*, Result 4):
+ *       (int |f''|^{2/5})^{5/2} / (N^2 sqrt(120))
+ *   form PWL_INTERP, uniform = 1 (Result 6):
+ *       (b - a)^2 ||f''|| / (N^2 sqrt(120)),  ||f''|| = sqrt(int f''^2)
+ *   form PWL_PROJECT: the same divided by sqrt(6) (Result 5; the per-interval
+ *       ratio of Results 2-3 holds on any partition).
+ *   int_f2_25, int_f2_sq  the two integrals of pwl_error_constants (>= 0)
+ *   a, b                  the interval (a < b, finite)
+ *   err_out               host, one double
+ * Asymptotic in N (large N); errors: PWL_EINVAL.                            */
+pwl_status pwl_predicted_error(double int_f2_25, double int_f2_sq, double a, double b, int64_t n_intervals,
+                               int32_t form, int32_t uniform, double* err_out);
+
+/* Smallest N whose predicted error (as pwl_predicted_error) is <= target_l2
+ * (host only).  n_out: host, one int64.  Errors: PWL_EINVAL (arguments, or a
+ * target needing more intervals than pwl_design accepts).                  */
+pwl_status pwl_n_for_error(double int_f2_25, double int_f2_sq, double a, double b, double target_l2, int32_t form,
+                           int32_t uniform, int64_t* n_out);
+
+/* ------------------------------------------------------------------------ */
 /* Device representation of a CPWL function (inputs of Algorithm 1)          */
 /* ------------------------------------------------------------------------ */
 

@@ -19,6 +19,7 @@ from ._capi import (DTYPES, FORMS, KINDS, PRECISIONS, PwlBatchInfo, PwlError, Pw
 __all__ = [
     "PwlError", "pwl_design", "pwl_project", "pwl_table_build", "pwl_table_update", "pwl_table_check", "pwl_table_destroy", "pwl_table_get_info",
     "pwl_eval", "pwl_eval_variant", "pwl_eval_synthetic", "pwl_eval_backward", "pwl_eval_backward_noalloc",
+    "pwl_error_constants", "pwl_predicted_error", "pwl_n_for_error",
     "pwl_batch_create", "pwl_batch_destroy", "pwl_batch_design", "pwl_batch_project", "pwl_batch_build",
     "pwl_batch_check", "pwl_batch_plan", "pwl_batch_eval", "pwl_batch_autotune", "pwl_batch_get_info", "Batch",
     "pwl_channels_forward", "pwl_channels_backward", "ChannelPWL", "Table", "design", "project", "PWLFunction",
@@ -173,6 +174,37 @@ def pwl_eval_synthetic(handle, m: int, seed: int = 0, out=None, stream=None):
     check(load().pwl_eval_synthetic(ctypes.c_void_p(handle), int(seed) & 0xFFFFFFFF, int(m), _ptr(out),
                                     _stream(stream)), "pwl_eval_synthetic")
     return out
+
+
+def pwl_error_constants(f, m_cells: int = 0, out=None, stream=None):
+    """The integrals of |f''|^{2/5} and f''^2 over [a, b] (Results 4-6),
+    midpoint rule on m_cells cells -> float64 (2,) on the GPU."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _require(out, torch.float64, "out", 2)
+    F = make_func(f)
+    check(load().pwl_error_constants(ctypes.byref(F), int(m_cells), _ptr(out), _stream(stream)),
+          "pwl_error_constants")
+    return out
+
+
+def pwl_predicted_error(int_f2_25: float, int_f2_sq: float, a: float, b: float, n_intervals: int,
+                        form: str = "interp", uniform: bool = False) -> float:
+    """Predicted L2 error with N intervals (Results 4-6)."""
+    r = ctypes.c_double()
+    check(load().pwl_predicted_error(float(int_f2_25), float(int_f2_sq), float(a), float(b), int(n_intervals),
+                                     FORMS[form], int(bool(uniform)), ctypes.byref(r)), "pwl_predicted_error")
+    return r.value
+
+
+def pwl_n_for_error(int_f2_25: float, int_f2_sq: float, a: float, b: float, target_l2: float,
+                    form: str = "interp", uniform: bool = False) -> int:
+    """Smallest N whose predicted L2 error is <= target_l2 (Results 4-6)."""
+    r = ctypes.c_int64()
+    check(load().pwl_n_for_error(float(int_f2_25), float(int_f2_sq), float(a), float(b), float(target_l2),
+                                 FORMS[form], int(bool(uniform)), ctypes.byref(r)), "pwl_n_for_error")
+    return r.value
 
 
 def pwl_eval_backward(handle, x, gy, gx=None, g_values=None, g_knots=None, workspace=None, stream=None):

@@ -71,6 +71,9 @@ SIGNATURES = {
     "pwl_eval": (_ST, [_P, _P, _P, _I64, _I32, _P]),
     "pwl_eval_variant": (_ST, [_P, _I32, _P, _P, _I64, _P]),
     "pwl_eval_synthetic": (_ST, [_P, ctypes.c_uint32, _I64, _P, _P]),
+    "pwl_error_constants": (_ST, [ctypes.POINTER(PwlFunc), _I64, _P, _P]),
+    "pwl_predicted_error": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_double)]),
+    "pwl_n_for_error": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I32, _I32, ctypes.POINTER(_I64)]),
     "pwl_eval_backward_workspace_size": (_SZ, [_P]),
     "pwl_eval_backward": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P, _SZ, _P]),
     "pwl_eval_backward_noalloc": (_ST, [_P, _P, _P, _P, _P, _P, _I64, _P]),
