@@ -54,13 +54,27 @@ typedef enum {
  *                    A = 1/(pi g) gives the paper's normalised form, Section V-B)
  *   PWL_F_BESSEL_J0  A J0(alpha x)                     p = {A, alpha}     (Section V-C)
  *   PWL_F_POLY       sum_{k=0..7} p[k] x^k                               (Fig. 1's quintic)
- *   PWL_F_EXP        A exp(lambda x)                   p = {A, lambda}                    */
+ *   PWL_F_EXP        A exp(lambda x)                   p = {A, lambda}
+ * and a function given by samples (any continuous f the caller can tabulate):
+ *   PWL_F_SAMPLED    S >= 4 FP64 samples s_j = f(a + j h), h = (b - a)/(S - 1),
+ *                    j = 0..S-1, in device memory that the caller keeps alive
+ *                    while calls use the descriptor; p[0] = S and p[1] holds
+ *                    the 64 bits of the device address (pwl_func_sampled
+ *                    writes both).  With u = (x - a)/h and
+ *                    j = min(max(floor(u), 1), S - 3):
+ *                      f(x)   = the cubic through samples j-1 .. j+2 at u;
+ *                      f''(x) = D_j + (u - j)(D_{j+1} - D_j), the linear
+ *                               interpolant (extrapolant in the end cells) of
+ *                               the second differences
+ *                               D_j = (s_{j-1} - 2 s_j + s_{j+1}) / h^2.
+ *                    Both are exact when f is a polynomial of degree <= 3.   */
 typedef enum {
     PWL_F_GAUSSIAN = 0,
     PWL_F_LORENTZIAN = 1,
     PWL_F_BESSEL_J0 = 2,
     PWL_F_POLY = 3,
-    PWL_F_EXP = 4
+    PWL_F_EXP = 4,
+    PWL_F_SAMPLED = 5
 } pwl_kind;
 
 typedef struct {
@@ -98,6 +112,12 @@ const char* pwl_last_error(void);
 
 /* ABI version (major * 10000 + minor * 100 + patch). */
 int32_t pwl_version(void);
+
+/* Fills *out with the descriptor of a sampled function (PWL_F_SAMPLED):
+ * n_samples >= 4 FP64 samples of f at a + j (b - a)/(n_samples - 1) in
+ * device memory (d_samples, 8-byte aligned, owned by the caller).  Host
+ * only; errors: PWL_EINVAL (NULL, n_samples < 4, a >= b, non-finite a, b).  */
+pwl_status pwl_func_sampled(double a, double b, const double* d_samples, int64_t n_samples, pwl_func* out);
 
 /* ------------------------------------------------------------------------ */
 /* Design: knots of the nearly optimal partition T* (Section III-B)          */

@@ -26,7 +26,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KINDS = {"gaussian": 0, "lorentzian": 1, "bessel_j0": 2, "poly": 3, "exp": 4}
+KINDS = {"gaussian": 0, "lorentzian": 1, "bessel_j0": 2, "poly": 3, "exp": 4, "sampled": 5}
 
 
 class _Func(ctypes.Structure):
@@ -89,6 +89,13 @@ def _func(desc) -> _Func:
     f.kind = KINDS[desc["kind"]]
     f.a = float(desc["a"])
     f.b = float(desc["b"])
+    if desc["kind"] == "sampled":
+        # host samples (numpy, FP64); the struct keeps them alive
+        s = np.ascontiguousarray(desc["samples"], dtype=np.float64)
+        f._samples = s
+        f.p[0] = float(s.size)
+        f.p[1] = np.frombuffer(np.uint64(s.ctypes.data).tobytes(), dtype=np.float64)[0]
+        return f
     p = list(desc.get("p", [])) + [0.0] * (8 - len(desc.get("p", [])))
     for i in range(8):
         f.p[i] = float(p[i])

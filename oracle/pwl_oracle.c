@@ -43,7 +43,9 @@
  *   LORENTZIAN : A / (1 + ((x-x0)/g)^2)            p = {A, x0, g}
  *   BESSEL_J0  : A J0(alpha x)                     p = {A, alpha}
  *   POLY       : sum_{k<=7} p[k] x^k
- *   EXP        : A exp(lambda x)                   p = {A, lambda}       */
+ *   EXP        : A exp(lambda x)                   p = {A, lambda}
+ *   SAMPLED    : S = p[0] samples f(a + j h), h = (b-a)/(S-1), j < S, at the
+ *                host address whose 64 bits p[1] holds                      */
 typedef struct {
     int32_t kind;
     int32_t pad;
@@ -51,7 +53,58 @@ typedef struct {
     double p[8];
 } orc_func;
 
-enum { ORC_GAUSSIAN = 0, ORC_LORENTZIAN = 1, ORC_BESSEL_J0 = 2, ORC_POLY = 3, ORC_EXP = 4 };
+enum { ORC_GAUSSIAN = 0, ORC_LORENTZIAN = 1, ORC_BESSEL_J0 = 2, ORC_POLY = 3, ORC_EXP = 4, ORC_SAMPLED = 5 };
+
+/* A sampled f: the samples and the cell of x.  With u = (x - a)/h the cell
+ * is j = floor(u) kept in [1, S-3], so that samples j-1 .. j+2 exist; t =
+ * u - j (outside [0, 1) only in the two end cells). */
+static const double* orc_samples(const orc_func* F)
+{
+    uint64_t addr;
+    memcpy(&addr, &F->p[1], sizeof(addr));
+    return (const double*)(uintptr_t)addr;
+}
+
+static int64_t orc_sample_cell(const orc_func* F, double x, double* t)
+{
+    int64_t S = (int64_t)F->p[0];
+    double h = (F->b - F->a) / (double)(S - 1);
+    double u = (x - F->a) / h;
+    int64_t j = (int64_t)floor(u);
+    if (j < 1) j = 1;
+    if (j > S - 3) j = S - 3;
+    *t = u - (double)j;
+    return j;
+}
+
+/* f: Lagrange's form of the cubic through (m, s_{j+m}), m = -1, 0, 1, 2 */
+static double orc_sampled_f(const orc_func* F, double x)
+{
+    double t;
+    int64_t j = orc_sample_cell(F, x, &t);
+    const double* s = orc_samples(F);
+    double y = 0.0;
+    for (int m = -1; m <= 2; ++m) {
+        double w = 1.0;
+        for (int k = -1; k <= 2; ++k)
+            if (k != m) w *= (t - (double)k) / (double)(m - k);
+        y += w * s[j + m];
+    }
+    return y;
+}
+
+/* f'': the second differences D_i = (s_{i-1} - 2 s_i + s_{i+1}) / h^2 at
+ * samples j and j+1, joined by a straight line */
+static double orc_sampled_f2(const orc_func* F, double x)
+{
+    double t;
+    int64_t j = orc_sample_cell(F, x, &t);
+    const double* s = orc_samples(F);
+    double h = (F->b - F->a) / (F->p[0] - 1.0);
+    double Dj = (s[j - 1] - 2.0 * s[j] + s[j + 1]) / (h * h);
+    double Dk = (s[j] - 2.0 * s[j + 1] + s[j + 2]) / (h * h);
+    return (1.0 - t) * Dj + t * Dk;
+}
 
 /* ------------------------------------------------------------------------ */
 /* f and f''                                                                 */
@@ -77,6 +130,8 @@ double orc_f(const orc_func* F, double x)
     }
     case ORC_EXP:
         return F->p[0] * exp(F->p[1] * x);
+    case ORC_SAMPLED:
+        return orc_sampled_f(F, x);
     }
     return NAN;
 }
@@ -116,6 +171,8 @@ double orc_f2(const orc_func* F, double x)
     }
     case ORC_EXP:
         return F->p[0] * F->p[1] * F->p[1] * exp(F->p[1] * x);
+    case ORC_SAMPLED:
+        return orc_sampled_f2(F, x);
     }
     return NAN;
 }

@@ -12,7 +12,7 @@ import threading
 from . import _build
 
 PWL_OK, PWL_EINVAL, PWL_ENOMEM, PWL_ECUDA, PWL_ENOTSUP, PWL_ETIMEOUT = range(6)
-KINDS = {"gaussian": 0, "lorentzian": 1, "bessel_j0": 2, "poly": 3, "exp": 4}
+KINDS = {"gaussian": 0, "lorentzian": 1, "bessel_j0": 2, "poly": 3, "exp": 4, "sampled": 5}
 FORMS = {"interp": 0, "project": 1}
 DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
@@ -59,6 +59,7 @@ _ST = ctypes.c_int
 SIGNATURES = {
     "pwl_last_error": (ctypes.c_char_p, []),
     "pwl_version": (_I32, []),
+    "pwl_func_sampled": (_ST, [ctypes.c_double, ctypes.c_double, _P, _I64, ctypes.POINTER(PwlFunc)]),
     "pwl_design_workspace_size": (_SZ, [_I64, _I64]),
     "pwl_design": (_ST, [ctypes.POINTER(PwlFunc), _I64, _I64, _I32, _P, _P, _SZ, _P]),
     "pwl_project_workspace_size": (_SZ, [_I64]),
@@ -126,6 +127,15 @@ def check(status: int, where: str) -> None:
 
 
 def make_func(desc) -> PwlFunc:
+    if desc["kind"] == "sampled":
+        # samples: a contiguous CUDA float64 tensor that the caller keeps alive
+        smp = desc["samples"]
+        if not (getattr(smp, "is_cuda", False) and str(smp.dtype) == "torch.float64" and smp.is_contiguous()):
+            raise TypeError("samples must be a contiguous CUDA float64 tensor")
+        f = PwlFunc()
+        check(load().pwl_func_sampled(float(desc["a"]), float(desc["b"]), ctypes.c_void_p(smp.data_ptr()),
+                                      smp.numel(), ctypes.byref(f)), "pwl_func_sampled")
+        return f
     f = PwlFunc()
     f.kind = KINDS[desc["kind"]]
     f.reserved = 0

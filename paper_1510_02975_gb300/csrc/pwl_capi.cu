@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <deque>
 #include <map>
@@ -107,12 +108,21 @@ cudaError_t occupancy_grid_fn(const void* fn, int threads, size_t smem, int* gri
 pwl_status validate_func(const pwl_func* f)
 {
     if (!f) return fail(PWL_EINVAL, "function descriptor is NULL");
-    if (f->kind < PWL_F_GAUSSIAN || f->kind > PWL_F_EXP)
+    if (f->kind < PWL_F_GAUSSIAN || f->kind > PWL_F_SAMPLED)
         return fail(PWL_EINVAL, "unknown function kind %d", f->kind);
     if (f->reserved != 0) return fail(PWL_EINVAL, "pwl_func.reserved must be 0");
     if (!isfinite(f->a) || !isfinite(f->b) || !(f->a < f->b))
         return fail(PWL_EINVAL, "interval [a, b] must be finite with a < b (got [%g, %g])", f->a,
                     f->b);
+    if (f->kind == PWL_F_SAMPLED) {
+        const double S = f->p[0];
+        if (!(S >= 4.0) || !(S <= 9007199254740992.0) || S != floor(S))
+            return fail(PWL_EINVAL, "a sampled function needs an integer sample count >= 4 in p[0]");
+        const uint64_t addr = sampled_address(*f);
+        if (addr == 0 || (addr & 7u) != 0)
+            return fail(PWL_EINVAL, "a sampled function needs an 8-byte aligned sample address in p[1]");
+        return PWL_OK;
+    }
     for (int i = 0; i < 8; ++i)
         if (!isfinite(f->p[i])) return fail(PWL_EINVAL, "parameter p[%d] is not finite", i);
     if ((f->kind == PWL_F_GAUSSIAN || f->kind == PWL_F_LORENTZIAN) && !(f->p[2] != 0.0))
@@ -122,7 +132,28 @@ pwl_status validate_func(const pwl_func* f)
 
 }  // namespace pwl
 
+using namespace pwl;
+
 extern "C" {
+
+pwl_status pwl_func_sampled(double a, double b, const double* d_samples, int64_t n_samples, pwl_func* out)
+{
+    clear_error();
+    if (!out) return fail(PWL_EINVAL, "out is NULL");
+    if (!d_samples) return fail(PWL_EINVAL, "d_samples is NULL");
+    if (n_samples < 4) return fail(PWL_EINVAL, "need at least 4 samples (got %lld)", (long long)n_samples);
+    if (!isfinite(a) || !isfinite(b) || !(a < b)) return fail(PWL_EINVAL, "need finite a < b");
+    pwl_func f;
+    memset(&f, 0, sizeof(f));
+    f.kind = PWL_F_SAMPLED;
+    f.a = a;
+    f.b = b;
+    f.p[0] = (double)n_samples;
+    const uint64_t addr = (uint64_t)(uintptr_t)d_samples;
+    memcpy(&f.p[1], &addr, sizeof(addr));
+    *out = f;
+    return validate_func(out);
+}
 
 const char* pwl_last_error(void) { return pwl::g_err; }
 

@@ -7,6 +7,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "pwl.h"
 #include "pwl_bessel.cuh"
@@ -74,6 +75,57 @@ struct FMath<float> {
     static __device__ __forceinline__ float pw(float x, float y) { return powf(x, y); }
 };
 
+// PWL_F_SAMPLED: p[0] = S, p[1] = the 64 bits of the samples' address
+__host__ __device__ __forceinline__ uint64_t sampled_address(const pwl_func& F)
+{
+    uint64_t a;
+    memcpy(&a, &F.p[1], sizeof(a));
+    return a;
+}
+
+// The sampled function's cell: u = (x - a)/h, j = min(max(floor(u), 1), S - 3).
+struct SampledCell {
+    const double* s;
+    int64_t j;
+    double t;  // u - j, in [-1, 2] after the clamp (the end cells extrapolate)
+    double inv_h2;
+};
+__device__ __forceinline__ SampledCell sampled_cell(const pwl_func& F, double x)
+{
+    const int64_t S = (int64_t)F.p[0];
+    const double h = (F.b - F.a) / (double)(S - 1);
+    const double u = (x - F.a) / h;
+    const double fu = floor(u);
+    const int64_t j = fu < 1.0 ? 1 : (fu > (double)(S - 3) ? S - 3 : (int64_t)fu);
+    SampledCell c;
+    c.s = reinterpret_cast<const double*>(sampled_address(F));
+    c.j = j;
+    c.t = u - (double)j;
+    c.inv_h2 = 1.0 / (h * h);
+    return c;
+}
+// f: the cubic through samples j-1 .. j+2 (Lagrange form, nodes -1, 0, 1, 2)
+__device__ __forceinline__ double sampled_value(const pwl_func& F, double x)
+{
+    const SampledCell c = sampled_cell(F, x);
+    const double t = c.t;
+    const double* s = c.s + c.j;
+    const double lm = -t * (t - 1.0) * (t - 2.0) / 6.0;
+    const double l0 = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+    const double l1 = -(t + 1.0) * t * (t - 2.0) / 2.0;
+    const double l2 = (t + 1.0) * t * (t - 1.0) / 6.0;
+    return lm * s[-1] + l0 * s[0] + l1 * s[1] + l2 * s[2];
+}
+// f'': second differences at samples j and j+1, linearly interpolated
+__device__ __forceinline__ double sampled_second_derivative(const pwl_func& F, double x)
+{
+    const SampledCell c = sampled_cell(F, x);
+    const double* s = c.s + c.j;
+    const double dj = (s[-1] - 2.0 * s[0] + s[1]) * c.inv_h2;
+    const double dk = (s[0] - 2.0 * s[1] + s[2]) * c.inv_h2;
+    return dj + c.t * (dk - dj);
+}
+
 // f(x) for the kinds of pwl_kind.
 template <typename T>
 __device__ __forceinline__ T func_value(const pwl_func& F, T x)
@@ -97,6 +149,8 @@ __device__ __forceinline__ T func_value(const pwl_func& F, T x)
     }
     case PWL_F_EXP:
         return (T)F.p[0] * M::ex((T)F.p[1] * x);
+    case PWL_F_SAMPLED:
+        return (T)sampled_value(F, (double)x);
     }
     return T(0);
 }
@@ -135,6 +189,8 @@ __device__ __forceinline__ T func_second_derivative(const pwl_func& F, T x)
     }
     case PWL_F_EXP:
         return (T)F.p[0] * (T)F.p[1] * (T)F.p[1] * M::ex((T)F.p[1] * x);
+    case PWL_F_SAMPLED:
+        return (T)sampled_second_derivative(F, (double)x);
     }
     return T(0);
 }
@@ -170,6 +226,8 @@ __device__ __forceinline__ FuncF make_funcf(const pwl_func& F)
         g.c[0] = (float)F.p[0];
         g.c[1] = (float)F.p[1];
         g.c[3] = (float)(F.p[0] * F.p[1] * F.p[1]);
+        break;
+    case PWL_F_SAMPLED:  // evaluated from the samples (sampled_second_derivative)
         break;
     default:  // PWL_F_POLY
         for (int k = 2; k < 8; ++k) g.d[k - 2] = (float)((double)(k * (k - 1)) * F.p[k]);

@@ -261,10 +261,13 @@ __device__ __forceinline__ double fused_density<double>(const pwl_func& F, doubl
 // hardware exp2/log2 pair (__powf), a few ulp (the FP32 mode's knot bound
 // allows a relative density error near 1e-6), for a third of the
 // instructions of powf
-__device__ __forceinline__ float fused_density_f(const FuncF& G, float t0f, float deltaf, int local)
+__device__ __forceinline__ float fused_density_f(const FuncF& G, const pwl_func& F, float t0f, float deltaf,
+                                                 int local)
 {
     const float t = __fmaf_rn((float)local + 0.5f, deltaf, t0f);
-    return __powf(fabsf(func_second_derivative_f(G, t)), 0.4f);
+    const float f2 = G.kind == PWL_F_SAMPLED ? (float)sampled_second_derivative(F, (double)t)
+                                             : func_second_derivative_f(G, t);
+    return __powf(fabsf(f2), 0.4f);
 }
 
 // smallest i in [1, N] with tau_i = i G_M / N >= G (N if none below N)
@@ -573,7 +576,7 @@ __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(De
             for (int r = 0; r < kPerThread; ++r) {
                 const int l = t * kPerThread + r;
                 if (l < cnt) {
-                    const float dk = fused_density_f(G, t0f, deltaf, l);
+                    const float dk = fused_density_f(G, F, t0f, deltaf, l);
                     dbuf[c0 + l] = dk;
                     part = ff_add(part, FF{dk, 0.0f});
                     if (dk > 0.0f) last = l;
