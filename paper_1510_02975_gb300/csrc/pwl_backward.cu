@@ -219,11 +219,13 @@ __global__ void backward_reduce_kernel(const float* __restrict__ partials, int r
 BwdShape backward_shape(pwl_table t)
 {
     BwdShape s{};
+    s.err = cudaSuccess;
     s.n_smem = backward_smem_records(t);
     if (s.n_smem < 0) return s;
     s.smem = backward_smem_bytes(t);
     s.threads = 1024;
-    if (occupancy_grid(backward_kernel, s.threads, s.smem, &s.grid) != cudaSuccess) {
+    s.err = occupancy_grid(backward_kernel, s.threads, s.smem, &s.grid);
+    if (s.err != cudaSuccess) {
         s.n_smem = -1;
         return s;
     }
@@ -313,9 +315,11 @@ pwl_status pwl_eval_backward_noalloc(pwl_table t, const float* d_x, const float*
     if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
     // device_info() of this device is already cached: pwl_table_build used it
     const BwdShape sh = backward_shape(t);
-    if (sh.n_smem < 0)
+    if (sh.n_smem < 0) {
+        if (sh.err != cudaSuccess) return cuda_fail(sh.err, "backward kernel launch shape");
         return fail(PWL_ENOTSUP, "backward stages 12 (N+2) bytes of shared memory; N = %lld is too large",
                     (long long)t->N);
+    }
     const int sms = device_info().sms;
     const int64_t row = 2 * (t->N + 2);
     const int64_t rows = (int64_t)(kStaticPartials / (size_t)row);
@@ -355,9 +359,11 @@ pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, f
     cudaGetDevice(&dev);
     if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
     const BwdShape sh = backward_shape(t);
-    if (sh.n_smem < 0)
-        return fail(PWL_ENOTSUP, "backward stages 12 (N+2) bytes of shared memory; N = %lld is too large (%s)",
-                    (long long)t->N, cudaGetErrorString(cudaGetLastError()));
+    if (sh.n_smem < 0) {
+        if (sh.err != cudaSuccess) return cuda_fail(sh.err, "backward kernel launch shape");
+        return fail(PWL_ENOTSUP, "backward stages 12 (N+2) bytes of shared memory; N = %lld is too large",
+                    (long long)t->N);
+    }
     if (!d_workspace || workspace_bytes < sh.workspace)
         return fail(PWL_EINVAL, "workspace of %zu bytes needed (got %zu)", sh.workspace, workspace_bytes);
     if (m == 0) return PWL_OK;

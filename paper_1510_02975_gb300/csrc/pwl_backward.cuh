@@ -11,6 +11,7 @@ struct BwdShape {
     int threads;
     int grid;          // persistent grid (maximum CTAs of one launch)
     size_t workspace;  // bytes of per-CTA partial sums for `grid` CTAs
+    cudaError_t err;   // the CUDA error that made n_smem -1, if any
 };
 
 BwdShape backward_shape(pwl_table t);

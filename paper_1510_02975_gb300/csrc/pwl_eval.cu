@@ -442,7 +442,8 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
     const int64_t units = p.nvec + (m - p.nvec * Vec<IO>::n);
     const int64_t per_cta = (int64_t)1024 * kUnroll;
     const int64_t spread = std::min<int64_t>(device_info().sms, (units + 255) / 256);
-    const int grid = (int)std::min<int64_t>(max_grid, std::max<int64_t>(spread, (units + per_cta - 1) / per_cta));
+    const int grid =
+        (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, std::max<int64_t>(spread, (units + per_cta - 1) / per_cta)));
     kern<<<grid, 1024, smem, s>>>(p, x, y, m);
     PWL_CHECK_LAUNCH("eval_kernel");
     return PWL_OK;
