@@ -32,11 +32,12 @@ namespace pwl {
 
 namespace {
 
-constexpr int kCh = 16;  // channels per tile
-constexpr int kChThreads = 1024;
-constexpr int kRowsPerPass = kChThreads / kCh;  // 64 rows per pass of the CTA
-constexpr int kChUnroll = 16;                    // passes in flight per thread (64 KB per SM)
-constexpr int kChTail = 3;
+constexpr int kChThreads = 1024;                 // threads per CTA, both directions
+// backward tiles (the forward's constants are kChF, kClF, kRowsPerPassF, ...)
+constexpr int kCh = 16;                          // channels per backward tile
+constexpr int kRowsPerPass = kChThreads / kCh;   // 64 rows per pass of the CTA
+constexpr int kChUnroll = 16;                    // loads in flight per thread (8 rows x, gy: 64 KB per SM)
+constexpr int kChTail = 3;                       // rows per predicated batch of a unit's tail
 
 struct TileParams {
     float a[kCh], b[kCh], inv_w[kCh], off[kCh], w[kCh];
