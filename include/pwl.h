@@ -58,9 +58,10 @@ typedef enum {
  * and a function given by samples (any continuous f the caller can tabulate):
  *   PWL_F_SAMPLED    S >= 4 FP64 samples s_j = f(a + j h), h = (b - a)/(S - 1),
  *                    j = 0..S-1, in device memory that the caller keeps alive
- *                    while calls use the descriptor; p[0] = S and p[1] holds
- *                    the 64 bits of the device address (pwl_func_sampled
- *                    writes both).  With u = (x - a)/h and
+ *                    while calls use the descriptor; p[0] = S, p[1] holds
+ *                    the 64 bits of the device address, p[2..4] = h, 1/h,
+ *                    1/h^2 (pwl_func_sampled writes them all).  With
+ *                    u = (x - a) (1/h) and
  *                    j = min(max(floor(u), 1), S - 3):
  *                      f(x)   = the cubic through samples j-1 .. j+2 at u;
  *                      f''(x) = D_j + (u - j)(D_{j+1} - D_j), the linear

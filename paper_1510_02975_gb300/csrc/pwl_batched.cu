@@ -485,6 +485,7 @@ using namespace pwl;
 struct pwl_batch_s {
     int device;
     int64_t F;
+    int kinds;                  // kKindsAnalytic | kKindsSampled of the functions
     int64_t m_per;
     std::vector<int64_t> N;     // intervals per function
     std::vector<int64_t> koff;  // knot offsets
@@ -640,6 +641,7 @@ pwl_status pwl_batch_create(const pwl_func* funcs, const int64_t* n_intervals, i
     cudaGetDevice(&b->device);
     const DeviceInfo& di = device_info();
     b->F = n_funcs;
+    b->kinds = kinds_of(funcs, n_funcs);
     b->m_per = mper;
     b->N.assign(n_intervals, n_intervals + n_funcs);
     b->koff.resize(n_funcs + 1);
@@ -747,6 +749,7 @@ pwl_status pwl_batch_design(pwl_batch b, int32_t precision, void* stream)
     DesignPlan p{};
     p.F = (int)b->F;
     p.precision = precision;
+    p.kinds = b->kinds;
     p.funcs = b->funcs;
     p.koff = b->d_koff;
     p.moff = b->d_moff;
@@ -774,6 +777,7 @@ pwl_status pwl_batch_project(pwl_batch b, int32_t form, int32_t quad_points, int
     ProjectPlan p{};
     p.F = (int)b->F;
     p.precision = precision;
+    p.kinds = b->kinds;
     p.form = form;
     p.max_rows = (int)(*std::max_element(b->N.begin(), b->N.end()) + 1);
     p.total_knots = b->total_knots;

@@ -121,6 +121,9 @@ pwl_status validate_func(const pwl_func* f)
         const uint64_t addr = sampled_address(*f);
         if (addr == 0 || (addr & 7u) != 0)
             return fail(PWL_EINVAL, "a sampled function needs an 8-byte aligned sample address in p[1]");
+        const double h = (f->b - f->a) / (S - 1.0);
+        if (f->p[2] != h || f->p[3] != 1.0 / h || f->p[4] != 1.0 / (h * h))
+            return fail(PWL_EINVAL, "a sampled function needs p[2..4] = h, 1/h, 1/h^2 (pwl_func_sampled)");
         return PWL_OK;
     }
     for (int i = 0; i < 8; ++i)
@@ -151,6 +154,10 @@ pwl_status pwl_func_sampled(double a, double b, const double* d_samples, int64_t
     f.p[0] = (double)n_samples;
     const uint64_t addr = (uint64_t)(uintptr_t)d_samples;
     memcpy(&f.p[1], &addr, sizeof(addr));
+    const double h = (b - a) / ((double)n_samples - 1.0);
+    f.p[2] = h;
+    f.p[3] = 1.0 / h;
+    f.p[4] = 1.0 / (h * h);
     *out = f;
     return validate_func(out);
 }

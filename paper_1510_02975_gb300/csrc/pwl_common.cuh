@@ -78,12 +78,18 @@ struct FMath<float> {
 // PWL_F_SAMPLED: p[0] = S, p[1] = the 64 bits of the samples' address
 __host__ __device__ __forceinline__ uint64_t sampled_address(const pwl_func& F)
 {
+#ifdef __CUDA_ARCH__
+    return (uint64_t)__double_as_longlong(F.p[1]);  // a register move: F stays in registers
+#else
     uint64_t a;
     memcpy(&a, &F.p[1], sizeof(a));
     return a;
+#endif
 }
 
-// The sampled function's cell: u = (x - a)/h, j = min(max(floor(u), 1), S - 3).
+// The sampled function's cell: u = (x - a)/h (as x - a times 1/h, p[3]),
+// j = min(max(floor(u), 1), S - 3).  No division on the device: h, 1/h and
+// 1/h^2 are in the descriptor (p[2..4], written by pwl_func_sampled).
 struct SampledCell {
     const double* s;
     int64_t j;
@@ -93,15 +99,14 @@ struct SampledCell {
 __device__ __forceinline__ SampledCell sampled_cell(const pwl_func& F, double x)
 {
     const int64_t S = (int64_t)F.p[0];
-    const double h = (F.b - F.a) / (double)(S - 1);
-    const double u = (x - F.a) / h;
+    const double u = (x - F.a) * F.p[3];
     const double fu = floor(u);
     const int64_t j = fu < 1.0 ? 1 : (fu > (double)(S - 3) ? S - 3 : (int64_t)fu);
     SampledCell c;
     c.s = reinterpret_cast<const double*>(sampled_address(F));
     c.j = j;
     c.t = u - (double)j;
-    c.inv_h2 = 1.0 / (h * h);
+    c.inv_h2 = F.p[4];
     return c;
 }
 // f: the cubic through samples j-1 .. j+2 (Lagrange form, nodes -1, 0, 1, 2)
@@ -126,9 +131,9 @@ __device__ __forceinline__ double sampled_second_derivative(const pwl_func& F, d
     return dj + c.t * (dk - dj);
 }
 
-// f(x) for the kinds of pwl_kind.
+// f(x) for the analytic kinds of pwl_kind.
 template <typename T>
-__device__ __forceinline__ T func_value(const pwl_func& F, T x)
+__device__ __forceinline__ T func_value_analytic(const pwl_func& F, T x)
 {
     using M = FMath<T>;
     switch (F.kind) {
@@ -149,8 +154,6 @@ __device__ __forceinline__ T func_value(const pwl_func& F, T x)
     }
     case PWL_F_EXP:
         return (T)F.p[0] * M::ex((T)F.p[1] * x);
-    case PWL_F_SAMPLED:
-        return (T)sampled_value(F, (double)x);
     }
     return T(0);
 }
@@ -159,7 +162,7 @@ __device__ __forceinline__ T func_value(const pwl_func& F, T x)
 // J0(alpha x): A alpha^2 (J1(z)/z - J0(z)) (Bessel's equation, limit 1/2 at 0);
 // polynomial and exponential by direct differentiation.
 template <typename T>
-__device__ __forceinline__ T func_second_derivative(const pwl_func& F, T x)
+__device__ __forceinline__ T func_second_derivative_analytic(const pwl_func& F, T x)
 {
     using M = FMath<T>;
     switch (F.kind) {
@@ -189,10 +192,35 @@ __device__ __forceinline__ T func_second_derivative(const pwl_func& F, T x)
     }
     case PWL_F_EXP:
         return (T)F.p[0] * (T)F.p[1] * (T)F.p[1] * M::ex((T)F.p[1] * x);
-    case PWL_F_SAMPLED:
-        return (T)sampled_second_derivative(F, (double)x);
     }
     return T(0);
+}
+
+// f and f'' of any kind, the sampled path chosen at compile time: hot loops
+// pick the instantiation once per function (or interval), so that the FP64
+// interpolation of sampled functions adds no registers to the analytic kinds'
+// loops; f and f'' choose at run time where that does not matter.
+template <bool SAMPLED, typename T>
+__device__ __forceinline__ T func_value_k(const pwl_func& F, T x)
+{
+    if constexpr (SAMPLED) return (T)sampled_value(F, (double)x);
+    else return func_value_analytic<T>(F, x);
+}
+template <bool SAMPLED, typename T>
+__device__ __forceinline__ T func_second_derivative_k(const pwl_func& F, T x)
+{
+    if constexpr (SAMPLED) return (T)sampled_second_derivative(F, (double)x);
+    else return func_second_derivative_analytic<T>(F, x);
+}
+template <typename T>
+__device__ __forceinline__ T func_value(const pwl_func& F, T x)
+{
+    return F.kind == PWL_F_SAMPLED ? func_value_k<true, T>(F, x) : func_value_k<false, T>(F, x);
+}
+template <typename T>
+__device__ __forceinline__ T func_second_derivative(const pwl_func& F, T x)
+{
+    return F.kind == PWL_F_SAMPLED ? func_second_derivative_k<true, T>(F, x) : func_second_derivative_k<false, T>(F, x);
 }
 
 // FP32 evaluation of f'' (the FP32 design mode) from constants converted

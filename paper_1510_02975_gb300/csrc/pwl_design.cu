@@ -76,29 +76,40 @@ __device__ __forceinline__ double block_exclusive_scan(double v, double* s_warp,
     return r;
 }
 
-template <typename T>
+// d_k for this thread's cells of the chunk at c0 (sum returned); the
+// sampled path is a template flag, chosen once per chunk
+template <typename T, bool SAMPLED>
+__device__ __forceinline__ double density_chunk(const pwl_func& F, int64_t c0, int64_t M, double delta,
+                                                double* __restrict__ d)
+{
+    double acc = 0.0;
+    for (int r = 0; r < kPerThread; ++r) {
+        const int64_t k = c0 + r * kDesignThreads + threadIdx.x;
+        if (k < M) {
+            // t_k = a + (k + 1/2) delta, rounded as written (no fused multiply-add)
+            const double t = __dadd_rn(F.a, __dmul_rn((double)k + 0.5, delta));
+            const T f2 = func_second_derivative_k<SAMPLED, T>(F, (T)t);
+            const double dk = (double)FMath<T>::pw(fabs(f2), T(0.4));
+            d[k] = dk;
+            acc += dk;
+        }
+    }
+    return acc;
+}
+
+template <typename T, bool SAMPLED>
 __global__ void __launch_bounds__(kDesignThreads) density_chunks_kernel(DesignPlan p)
 {
     __shared__ double s_red[kDesignThreads / 32];
     for (int64_t ch = blockIdx.x; ch < p.total_chunks; ch += gridDim.x) {
         const int f = find_segment(p.choff, p.F, ch);
         const pwl_func F = p.funcs[f];
+        if ((F.kind == PWL_F_SAMPLED) != SAMPLED) continue;  // the other launch's (uniform per CTA)
         const int64_t M = p.moff[f + 1] - p.moff[f];
         const int64_t c0 = (ch - p.choff[f]) * kChunk;
         const double delta = (F.b - F.a) / (double)M;
         double* __restrict__ d = p.d + p.moff[f];
-        double acc = 0.0;
-        for (int r = 0; r < kPerThread; ++r) {
-            const int64_t k = c0 + r * kDesignThreads + threadIdx.x;
-            if (k < M) {
-                // t_k = a + (k + 1/2) delta, rounded as written (no fused multiply-add)
-                const double t = __dadd_rn(F.a, __dmul_rn((double)k + 0.5, delta));
-                const T f2 = func_second_derivative<T>(F, (T)t);
-                const double dk = (double)FMath<T>::pw(fabs(f2), T(0.4));
-                d[k] = dk;
-                acc += dk;
-            }
-        }
+        double acc = density_chunk<T, SAMPLED>(F, c0, M, delta, d);
         acc = warp_sum(acc);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
         __syncthreads();
@@ -247,28 +258,46 @@ struct Partial<float> {
 __device__ __forceinline__ double approx(const Partial<double>& p) { return p.s; }
 __device__ __forceinline__ float approx(const Partial<float>& p) { return p.s; }
 
-template <typename T>
-__device__ __forceinline__ T fused_density(const pwl_func& F, double a, double delta, int64_t k, float t0f,
-                                           float deltaf, int local);
-template <>
-__device__ __forceinline__ double fused_density<double>(const pwl_func& F, double a, double delta, int64_t k,
-                                                        float, float, int)
+// FP64 density of cell k: |f''(t_k)|^{2/5}, t_k = a + (k + 1/2) delta
+template <bool SAMPLED>
+__device__ __forceinline__ double fused_density64(const pwl_func& F, double a, double delta, int64_t k)
 {
     const double t = __dadd_rn(a, __dmul_rn((double)k + 0.5, delta));
-    return pow(fabs(func_second_derivative<double>(F, t)), 0.4);
+    return pow(fabs(func_second_derivative_k<SAMPLED, double>(F, t)), 0.4);
+}
+
+// The densities of one chunk's cells of this thread, added to `part`; STORE
+// keeps them in s_d, LAST tracks the last cell of positive density.  The
+// sampled path is a template flag, chosen once per chunk.
+template <bool SAMPLED, bool STORE, bool LAST>
+__device__ __forceinline__ void fused_chunk64(const pwl_func& F, double a, double delta, int64_t c0, int cnt,
+                                              Partial<double>& part, int& last, double* s_d)
+{
+    for (int r = 0; r < kPerThread; ++r) {
+        const int l = threadIdx.x * kPerThread + r;
+        if (l < cnt) {
+            const double dk = fused_density64<SAMPLED>(F, a, delta, c0 + l);
+            if (STORE) s_d[l] = dk;
+            part.add(dk);
+            if (LAST && dk > 0.0) last = l;
+        }
+    }
 }
 // FP32 density from the function's FP32 constants: |f''|^{2/5} by the
 // hardware exp2/log2 pair (__powf), a few ulp (the FP32 mode's knot bound
 // allows a relative density error near 1e-6), for a third of the
 // instructions of powf
+template <bool SAMPLED>
 __device__ __forceinline__ float fused_density_f(const FuncF& G, const pwl_func& F, float t0f, float deltaf,
                                                  int local)
 {
     const float t = __fmaf_rn((float)local + 0.5f, deltaf, t0f);
-    const float f2 = G.kind == PWL_F_SAMPLED ? (float)sampled_second_derivative(F, (double)t)
-                                             : func_second_derivative_f(G, t);
+    float f2;
+    if constexpr (SAMPLED) f2 = (float)sampled_second_derivative(F, (double)t);
+    else f2 = func_second_derivative_f(G, t);
     return __powf(fabsf(f2), 0.4f);
 }
+
 
 // smallest i in [1, N] with tau_i = i G_M / N >= G (N if none below N)
 __device__ __forceinline__ int64_t first_target_at_or_above(double G, double GM, int64_t N)
@@ -281,7 +310,7 @@ __device__ __forceinline__ int64_t first_target_at_or_above(double G, double GM,
     return i;
 }
 
-template <typename T>
+template <typename T, bool SAMPLED>
 __global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan p)
 {
     __shared__ T s_d[kChunk];
@@ -294,6 +323,7 @@ __global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan
     for (int o = blockIdx.x; o < p.F; o += gridDim.x) {
         const int f = p.order[o];
         const pwl_func F = p.funcs[f];
+        if ((F.kind == PWL_F_SAMPLED) != SAMPLED) continue;  // the other launch's (uniform per CTA)
         const int64_t M = p.moff[f + 1] - p.moff[f];
         const int64_t N = p.koff[f + 1] - p.koff[f] - 1;
         const int64_t nch = p.choff[f + 1] - p.choff[f];
@@ -312,14 +342,7 @@ __global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan
             const float t0f = (float)(a + (double)c0 * delta);
             Partial<T> part;
             int last = -1;
-            for (int r = 0; r < kPerThread; ++r) {
-                const int l = t * kPerThread + r;
-                if (l < cnt) {
-                    const T dk = fused_density<T>(F, a, delta, c0 + l, t0f, deltaf, l);
-                    part.add(dk);
-                    if (dk > T(0)) last = l;
-                }
-            }
+            fused_chunk64<SAMPLED, false, true>(F, a, delta, c0, cnt, part, last, nullptr);
             if (t == 0) s_last = -1;
             __syncthreads();
             if (last >= 0) atomicMax(&s_last, last);
@@ -367,14 +390,8 @@ __global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan
                 const int cnt = (int)min((int64_t)kChunk, M - c0);
                 const float t0f = (float)(a + (double)c0 * delta);
                 Partial<T> part;
-                for (int r = 0; r < kPerThread; ++r) {
-                    const int l = t * kPerThread + r;
-                    if (l < cnt) {
-                        const T dk = fused_density<T>(F, a, delta, c0 + l, t0f, deltaf, l);
-                        s_d[l] = dk;
-                        part.add(dk);
-                    }
-                }
+                int unused = -1;
+                fused_chunk64<SAMPLED, true, false>(F, a, delta, c0, cnt, part, unused, s_d);
                 double tot;
                 const double ex = block_exclusive_scan(part.value(), s_warp, &tot);
                 s_S[t] = cbase[ch] + ex;
@@ -537,6 +554,26 @@ __device__ __forceinline__ int64_t first_target_at_or_above_units(double S, doub
     return i;
 }
 
+// The densities of one chunk into scratch, with the float-float total of the
+// thread's cells and its last cell of positive density.  Sampled functions
+// take a loop of their own, so that their FP64 interpolation does not weigh
+// on the registers of the analytic kinds' loop.
+template <bool SAMPLED>
+__device__ __forceinline__ void chunk_densities_f(const FuncF& G, const pwl_func& F, float t0f, float deltaf,
+                                                  int cnt, float* __restrict__ dchunk, FF& part, int& last)
+{
+    for (int r = 0; r < kPerThread; ++r) {
+        const int l = threadIdx.x * kPerThread + r;
+        if (l < cnt) {
+            const float dk = fused_density_f<SAMPLED>(G, F, t0f, deltaf, l);
+            dchunk[l] = dk;
+            part = ff_add(part, FF{dk, 0.0f});
+            if (dk > 0.0f) last = l;
+        }
+    }
+}
+
+template <bool SAMPLED>
 __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(DesignPlan p)
 {
     __shared__ float s_d[kChunk];
@@ -553,6 +590,7 @@ __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(De
     for (int o = blockIdx.x; o < p.F; o += gridDim.x) {
         const int f = p.order[o];
         const pwl_func F = p.funcs[f];
+        if ((F.kind == PWL_F_SAMPLED) != SAMPLED) continue;  // the other launch's (uniform per CTA)
         const FuncF G = make_funcf(F);  // FP32 constants of f'', once per function
         const int64_t M = p.moff[f + 1] - p.moff[f];
         const int64_t N = p.koff[f + 1] - p.koff[f] - 1;
@@ -573,15 +611,7 @@ __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(De
             const float t0f = (float)(a + (double)c0 * delta);
             FF part{0.0f, 0.0f};
             int last = -1;
-            for (int r = 0; r < kPerThread; ++r) {
-                const int l = t * kPerThread + r;
-                if (l < cnt) {
-                    const float dk = fused_density_f(G, F, t0f, deltaf, l);
-                    dbuf[c0 + l] = dk;
-                    part = ff_add(part, FF{dk, 0.0f});
-                    if (dk > 0.0f) last = l;
-                }
-            }
+            chunk_densities_f<SAMPLED>(G, F, t0f, deltaf, cnt, dbuf + c0, part, last);
             // chunk total and last positive cell: one barrier per chunk (the
             // slot pair alternates so that a chunk's writes never meet the
             // previous chunk's reads)
@@ -736,11 +766,21 @@ pwl_status design_launch(const DesignPlan& p, cudaStream_t s)
 {
     const DeviceInfo& di = device_info();
     const int grid_chunks = (int)std::min<int64_t>(p.total_chunks, (int64_t)di.sms * 8);
-    if (p.precision == PWL_PREC_FP32)
-        density_chunks_kernel<float><<<grid_chunks, kDesignThreads, 0, s>>>(p);
-    else
-        density_chunks_kernel<double><<<grid_chunks, kDesignThreads, 0, s>>>(p);
-    PWL_CHECK_LAUNCH("density_chunks_kernel");
+    const int kinds = plan_kinds(p.kinds);
+    if (kinds & kKindsAnalytic) {
+        if (p.precision == PWL_PREC_FP32)
+            density_chunks_kernel<float, false><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+        else
+            density_chunks_kernel<double, false><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+        PWL_CHECK_LAUNCH("density_chunks_kernel");
+    }
+    if (kinds & kKindsSampled) {
+        if (p.precision == PWL_PREC_FP32)
+            density_chunks_kernel<float, true><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+        else
+            density_chunks_kernel<double, true><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+        PWL_CHECK_LAUNCH("density_chunks_kernel");
+    }
     chunk_scan_kernel<<<(int)std::min<int64_t>(p.F, 65535), kDesignThreads, 0, s>>>(p);
     PWL_CHECK_LAUNCH("chunk_scan_kernel");
     cumulative_kernel<<<grid_chunks, kDesignThreads, 0, s>>>(p);
@@ -755,11 +795,21 @@ pwl_status design_fused_launch(const DesignPlan& p, cudaStream_t s)
 {
     const DeviceInfo& di = device_info();
     const int grid = (int)std::min<int64_t>(p.F, (int64_t)di.sms * 8);
-    if (p.precision == PWL_PREC_FP32)
-        design_fused_fp32_kernel<<<grid, kDesignThreads, 0, s>>>(p);
-    else
-        design_fused_kernel<double><<<grid, kDesignThreads, 0, s>>>(p);
-    PWL_CHECK_LAUNCH("design_fused_kernel");
+    const int kinds = plan_kinds(p.kinds);
+    if (kinds & kKindsAnalytic) {
+        if (p.precision == PWL_PREC_FP32)
+            design_fused_fp32_kernel<false><<<grid, kDesignThreads, 0, s>>>(p);
+        else
+            design_fused_kernel<double, false><<<grid, kDesignThreads, 0, s>>>(p);
+        PWL_CHECK_LAUNCH("design_fused_kernel");
+    }
+    if (kinds & kKindsSampled) {
+        if (p.precision == PWL_PREC_FP32)
+            design_fused_fp32_kernel<true><<<grid, kDesignThreads, 0, s>>>(p);
+        else
+            design_fused_kernel<double, true><<<grid, kDesignThreads, 0, s>>>(p);
+        PWL_CHECK_LAUNCH("design_fused_kernel");
+    }
     return PWL_OK;
 }
 
@@ -805,6 +855,7 @@ pwl_status pwl_design(const pwl_func* f, int64_t n_intervals, int64_t m_cells, i
     char* w = static_cast<char*>(d_workspace);
     DesignPlan p{};
     p.F = 1;
+    p.kinds = kinds_of(f, 1);
     p.funcs = reinterpret_cast<pwl_func*>(w);
     p.koff = reinterpret_cast<int64_t*>(w + 128);
     p.moff = reinterpret_cast<int64_t*>(w + 160);

@@ -11,9 +11,24 @@ constexpr int kMaxIntervals = 1048575;
 // F functions; function f owns knots koff[f] .. koff[f+1]-1 (N_f + 1 of them),
 // density cells moff[f] .. moff[f+1]-1 (M_f), chunks choff[f] .. choff[f+1]-1,
 // and G entries moff[f] + f .. moff[f+1] + f (M_f + 1).
+// Which kinds a plan holds: the hot kernels are compiled once for the
+// analytic kinds and once for sampled functions (whose FP64 interpolation
+// would otherwise weigh on the analytic loops' registers); a launch runs the
+// instantiations its plan needs.  0 means both.
+constexpr int kKindsAnalytic = 1;
+constexpr int kKindsSampled = 2;
+inline int plan_kinds(int kinds) { return kinds ? kinds : (kKindsAnalytic | kKindsSampled); }
+inline int kinds_of(const pwl_func* f, int64_t n)
+{
+    int k = 0;
+    for (int64_t i = 0; i < n; ++i) k |= f[i].kind == PWL_F_SAMPLED ? kKindsSampled : kKindsAnalytic;
+    return k;
+}
+
 struct DesignPlan {
     int F;
     int precision;
+    int kinds;  // kKindsAnalytic | kKindsSampled of the functions (0: both)
     const pwl_func* funcs;
     const int64_t* koff;
     const int64_t* moff;
@@ -43,6 +58,7 @@ pwl_status design_fused_launch(const DesignPlan& p, cudaStream_t s);
 struct ProjectPlan {
     int F;
     int precision;
+    int kinds;  // kKindsAnalytic | kKindsSampled of the functions (0: both)
     int form;
     int max_rows;          // max over f of N_f + 1
     int64_t total_knots;

@@ -22,6 +22,7 @@ namespace {
 constexpr int kConstThreads = 256;
 
 // out[0] += delta * sum_k |f''(t_k)|^{2/5}, out[1] += delta * sum_k f''(t_k)^2
+template <bool SAMPLED>
 __global__ void __launch_bounds__(kConstThreads) error_constants_kernel(pwl_func F, int64_t M, double* out)
 {
     __shared__ double s_red[2][kConstThreads / 32];
@@ -30,7 +31,7 @@ __global__ void __launch_bounds__(kConstThreads) error_constants_kernel(pwl_func
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M; k += stride) {
         const double t = __dadd_rn(F.a, __dmul_rn((double)k + 0.5, delta));
-        const double f2 = func_second_derivative<double>(F, t);
+        const double f2 = func_second_derivative_k<SAMPLED, double>(F, t);
         s25 += pow(fabs(f2), 0.4);
         s2 = __fma_rn(f2, f2, s2);
     }
@@ -90,7 +91,10 @@ pwl_status pwl_error_constants(const pwl_func* f, int64_t m_cells, double* d_out
     cudaStream_t s = as_stream(stream);
     PWL_CUDA_TRY(cudaMemsetAsync(d_out, 0, 2 * sizeof(double), s));
     const int64_t blocks = std::min<int64_t>((M + kConstThreads - 1) / kConstThreads, (int64_t)device_info().sms * 8);
-    error_constants_kernel<<<(int)blocks, kConstThreads, 0, s>>>(*f, M, d_out);
+    if (f->kind == PWL_F_SAMPLED)
+        error_constants_kernel<true><<<(int)blocks, kConstThreads, 0, s>>>(*f, M, d_out);
+    else
+        error_constants_kernel<false><<<(int)blocks, kConstThreads, 0, s>>>(*f, M, d_out);
     PWL_CHECK_LAUNCH("error_constants_kernel");
     return PWL_OK;
 }

@@ -46,13 +46,15 @@ __device__ __forceinline__ int find_knot_owner(const int64_t* __restrict__ koff,
     return lo;
 }
 
-template <typename T>
+template <typename T, bool SAMPLED>
 __global__ void interp_values_kernel(ProjectPlan p)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < p.total_knots; g += stride) {
         const int f = find_knot_owner(p.koff, p.F, g);
-        p.values[g] = (double)func_value<T>(p.funcs[f], (T)p.knots[g]);
+        const pwl_func F = p.funcs[f];
+        if ((F.kind == PWL_F_SAMPLED) != SAMPLED) continue;  // the other launch's
+        p.values[g] = (double)func_value_k<SAMPLED, T>(F, (T)p.knots[g]);
     }
 }
 
@@ -63,7 +65,47 @@ __global__ void interp_values_kernel(ProjectPlan p)
 // division per node.  FP64 mode: t_q and the sums in FP64.  FP32 mode: t_q
 // and f(t_q) in FP32 (the argument of an FP32 f is rounded to FP32 anyway),
 // the sums in FP64.
-template <typename T>
+// sum_q wl_q f(t_q) and sum_q wr_q f(t_q) over one interval (the half-length
+// factor applied by the caller); the sampled path is a template flag,
+// chosen once per interval
+template <typename T, bool SAMPLED>
+__device__ __forceinline__ void hat_sums(const pwl_func& F, const GaussLegendre& gl, double mid, double half,
+                                         double& L, double& R)
+{
+    if constexpr (sizeof(T) == 4) {
+        // sums of w f(t) as float-float pairs: each product exact (the
+        // weight split hi + lo, the rounding error of hi f recovered by an
+        // FMA), each addition compensated; FP64 once per interval
+        const float midf = (float)mid, halff = (float)half;
+        float Lh = 0.0f, Ll = 0.0f, Rh = 0.0f, Rl = 0.0f;
+        auto acc = [](float& h, float& l, float wh, float wlo, float fv) {
+            const float p = __fmul_rn(wh, fv);
+            const float pe = __fmaf_rn(wh, fv, -p) + __fmul_rn(wlo, fv);  // hi f - p exactly, plus lo f
+            const float s = __fadd_rn(h, p);
+            const float bp = __fsub_rn(s, h);
+            const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+            h = s;
+            l = __fadd_rn(l, __fadd_rn(e, pe));
+        };
+        for (int q = 0; q < gl.Q; ++q) {
+            const float fv = func_value_k<SAMPLED, float>(F, __fmaf_rn(halff, gl.xf[q], midf));
+            acc(Lh, Ll, gl.wlh[q], gl.wll[q], fv);
+            acc(Rh, Rl, gl.wrh[q], gl.wrl[q], fv);
+        }
+        L = (double)Lh + (double)Ll;
+        R = (double)Rh + (double)Rl;
+    } else {
+        L = 0.0;
+        R = 0.0;
+        for (int q = 0; q < gl.Q; ++q) {
+            const double fv = func_value_k<SAMPLED, double>(F, __fma_rn(half, gl.x[q], mid));
+            L = __fma_rn(gl.wl[q], fv, L);
+            R = __fma_rn(gl.wr[q], fv, R);
+        }
+    }
+}
+
+template <typename T, bool SAMPLED>
 __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ GaussLegendre gl)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -75,36 +117,9 @@ __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ Gaus
         const double xl = x[j - 1], xr = x[j];
         const double mid = 0.5 * (xl + xr), half = 0.5 * (xr - xl);
         const pwl_func F = p.funcs[f];
-        double L = 0.0, R = 0.0;
-        if constexpr (sizeof(T) == 4) {
-            // sums of w f(t) as float-float pairs: each product exact (the
-            // weight split hi + lo, the rounding error of hi f recovered by an
-            // FMA), each addition compensated; FP64 once per interval
-            const float midf = (float)mid, halff = (float)half;
-            float Lh = 0.0f, Ll = 0.0f, Rh = 0.0f, Rl = 0.0f;
-            auto acc = [](float& h, float& l, float wh, float wlo, float fv) {
-                const float p = __fmul_rn(wh, fv);
-                const float pe = __fmaf_rn(wh, fv, -p) + __fmul_rn(wlo, fv);  // hi f - p exactly, plus lo f
-                const float s = __fadd_rn(h, p);
-                const float bp = __fsub_rn(s, h);
-                const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-                h = s;
-                l = __fadd_rn(l, __fadd_rn(e, pe));
-            };
-            for (int q = 0; q < gl.Q; ++q) {
-                const float fv = func_value<float>(F, __fmaf_rn(halff, gl.xf[q], midf));
-                acc(Lh, Ll, gl.wlh[q], gl.wll[q], fv);
-                acc(Rh, Rl, gl.wrh[q], gl.wrl[q], fv);
-            }
-            L = (double)Lh + (double)Ll;
-            R = (double)Rh + (double)Rl;
-        } else {
-            for (int q = 0; q < gl.Q; ++q) {
-                const double fv = func_value<double>(F, __fma_rn(half, gl.x[q], mid));
-                L = __fma_rn(gl.wl[q], fv, L);
-                R = __fma_rn(gl.wr[q], fv, R);
-            }
-        }
+        if ((F.kind == PWL_F_SAMPLED) != SAMPLED) continue;  // the other launch's
+        double L, R;
+        hat_sums<T, SAMPLED>(F, gl, mid, half, L, R);
         p.lr[g] = make_double2(half * L, half * R);
     }
 }
@@ -393,19 +408,39 @@ pwl_status project_launch(const ProjectPlan& p, const GaussLegendre& gl, cudaStr
     const DeviceInfo& di = device_info();
     if (p.form == PWL_INTERP) {
         const int grid = (int)std::min<int64_t>((p.total_knots + 255) / 256, (int64_t)di.sms * 16);
-        if (p.precision == PWL_PREC_FP32)
-            interp_values_kernel<float><<<grid, 256, 0, s>>>(p);
-        else
-            interp_values_kernel<double><<<grid, 256, 0, s>>>(p);
-        PWL_CHECK_LAUNCH("interp_values_kernel");
+        const int kinds = plan_kinds(p.kinds);
+        if (kinds & kKindsAnalytic) {
+            if (p.precision == PWL_PREC_FP32)
+                interp_values_kernel<float, false><<<grid, 256, 0, s>>>(p);
+            else
+                interp_values_kernel<double, false><<<grid, 256, 0, s>>>(p);
+            PWL_CHECK_LAUNCH("interp_values_kernel");
+        }
+        if (kinds & kKindsSampled) {
+            if (p.precision == PWL_PREC_FP32)
+                interp_values_kernel<float, true><<<grid, 256, 0, s>>>(p);
+            else
+                interp_values_kernel<double, true><<<grid, 256, 0, s>>>(p);
+            PWL_CHECK_LAUNCH("interp_values_kernel");
+        }
         return PWL_OK;
     }
     const int grid = (int)std::min<int64_t>((p.total_intervals + 127) / 128, (int64_t)di.sms * 16);
-    if (p.precision == PWL_PREC_FP32)
-        hat_integrals_kernel<float><<<grid, 128, 0, s>>>(p, gl);
-    else
-        hat_integrals_kernel<double><<<grid, 128, 0, s>>>(p, gl);
-    PWL_CHECK_LAUNCH("hat_integrals_kernel");
+    const int kinds = plan_kinds(p.kinds);
+    if (kinds & kKindsAnalytic) {
+        if (p.precision == PWL_PREC_FP32)
+            hat_integrals_kernel<float, false><<<grid, 128, 0, s>>>(p, gl);
+        else
+            hat_integrals_kernel<double, false><<<grid, 128, 0, s>>>(p, gl);
+        PWL_CHECK_LAUNCH("hat_integrals_kernel");
+    }
+    if (kinds & kKindsSampled) {
+        if (p.precision == PWL_PREC_FP32)
+            hat_integrals_kernel<float, true><<<grid, 128, 0, s>>>(p, gl);
+        else
+            hat_integrals_kernel<double, true><<<grid, 128, 0, s>>>(p, gl);
+        PWL_CHECK_LAUNCH("hat_integrals_kernel");
+    }
     if (p.solver == 1) {
         // two warps (functions) per CTA, so that a few hundred functions
         // still spread over every SM
@@ -465,6 +500,7 @@ pwl_status pwl_project(const pwl_func* f, const double* d_knots, int64_t n_inter
     char* w = static_cast<char*>(d_workspace);
     ProjectPlan p{};
     p.F = 1;
+    p.kinds = kinds_of(f, 1);
     p.precision = precision;
     p.form = form;
     p.max_rows = (int)(n_intervals + 1);
