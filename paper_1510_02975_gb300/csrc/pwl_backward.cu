@@ -13,9 +13,10 @@
 // reciprocal lengths, streams (x, gy) -> gx with 16-byte vectors, and
 // accumulates A, B in shared memory with FP32 atomics; it then writes its
 // partial sums to the workspace (one row per CTA).
-// Pass 2: one thread per knot sums the CTA rows in a fixed order (FP64) and
-// forms g_v and g_x (the order of the in-CTA atomics still varies from run
-// to run, so the sums are reproducible to FP32 rounding, not bit for bit).
+// Pass 2: 32 knots per CTA, the CTA rows split over 16 thread groups, sums
+// the rows in a fixed order (FP64) and forms g_v and g_x (the order of the
+// in-CTA atomics still varies from run to run, so the sums are reproducible
+// to FP32 rounding, not bit for bit).
 #include <math.h>
 
 #include <algorithm>
@@ -56,13 +57,13 @@ struct EndSums {
 
 // One query, without branches apart from chain walks: the lookup runs on the
 // clamped point (a NaN looks up a and contributes nothing), the interval and
-// the side come from selects, and one predicated pair of shared-memory
-// atomics takes an interior query's two sums (a divergent version issued the
-// atomics once per path: 4x the atomic instructions).
+// the side come from selects.  An interior query returns its interval in
+// `bin` and its two sums gy (1 - delta), gy delta in ca, cb; any other query
+// returns bin = -1 (the ends are summed in registers).
 template <bool CHAINS>
-__device__ __forceinline__ float bwd_one(float x, float g, const float4* __restrict__ srec,
-                                         const float* __restrict__ s_ih, float* accA, float* accB,
-                                         EndSums& e, const BwdArgs& p, int copy)
+__device__ __forceinline__ float bwd_query(float x, float g, const float4* __restrict__ srec,
+                                           const float* __restrict__ s_ih, EndSums& e, const BwdArgs& p, int& bin,
+                                           float& ca, float& cb)
 {
     const float xc = fminf(fmaxf(x, p.a), p.b);  // NaN -> a
     const int c = cell_of(xc, p.inv_w, p.off, p.K);
@@ -87,10 +88,9 @@ __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restr
     const float delta = lside ? 1.0f - tt : tt;
     const float one_minus = lside ? tt : 1.0f - tt;
     const bool interior = x > p.a && x < p.b;  // false for NaN
-    if (interior) {
-        atomicAdd(accA + i * p.lanes + copy, g * one_minus);
-        atomicAdd(accB + i * p.lanes + copy, g * delta);
-    }
+    bin = interior ? i : -1;
+    ca = g * one_minus;
+    cb = g * delta;
     // the ends: clamped queries feed g_v[0] or g_v[N]; x = a is interval 1 at
     // delta = 0, x = b interval N at delta = 1
     e.clamped_left += x < p.a ? g : 0.0f;
@@ -103,6 +103,116 @@ __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restr
     return x != x ? x : gx;
 }
 
+// A query's two sums into its lane's accumulator copy (one predicated pair
+// of shared-memory atomics; a divergent version issued them once per path)
+__device__ __forceinline__ void bwd_scatter(float* accA, float* accB, int bin, float ca, float cb, int lanes,
+                                            int copy)
+{
+    if (bin >= 0) {
+        atomicAdd(accA + bin * lanes + copy, ca);
+        atomicAdd(accB + bin * lanes + copy, cb);
+    }
+}
+
+template <bool CHAINS>
+__device__ __forceinline__ float bwd_one(float x, float g, const float4* __restrict__ srec,
+                                         const float* __restrict__ s_ih, float* accA, float* accB,
+                                         EndSums& e, const BwdArgs& p, int copy)
+{
+    int bin;
+    float ca, cb;
+    const float gx = bwd_query<CHAINS>(x, g, srec, s_ih, e, p, bin, ca, cb);
+    bwd_scatter(accA, accB, bin, ca, cb, p.lanes, copy);
+    return gx;
+}
+
+// Whether every query of the warp's vector (four per lane, 128 in all) is
+// interior and lies in the interval of the warp's first query (bF) or of its
+// last (bL).  The first vote, on one query per lane, fails at once for random
+// queries; both votes are warp-uniform.
+__device__ __forceinline__ bool warp_two_bins(const int (&bin)[4], int& bF, int& bL)
+{
+    bF = __shfl_sync(0xffffffffu, bin[0], 0);
+    bL = __shfl_sync(0xffffffffu, bin[3], 31);
+    if (!__all_sync(0xffffffffu, bin[0] >= 0 && (bin[0] == bF || bin[0] == bL))) return false;
+    bool ok = true;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) ok = ok && bin[k] >= 0 && (bin[k] == bF || bin[k] == bL);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Four consecutive queries per lane, 128 per warp, all 32 lanes active.
+// Warp-aggregated scatter-add for sorted or clustered queries, where per-lane
+// atomics would all hit one or two addresses and serialise: when the whole
+// vector lies in intervals bF and bL, the warp sums the two intervals' A and
+// B by shuffles and lanes 0 and 1 add them with four atomics.  A warp runs in
+// one of two modes (`agg`, warp-uniform).  Per lane: each query's atomics
+// are issued right after its lookup, and on `detect` vectors a single vote
+// (is every lane's first query interior and in the warp's first interval?)
+// switches to the aggregated mode.  Aggregated: the vector's lookups come
+// first, and a vector that spans more intervals falls back to per-lane
+// atomics and switches back.
+template <bool CHAINS>
+__device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float4* __restrict__ srec,
+                                               const float* __restrict__ s_ih, float* accA, float* accB,
+                                               EndSums& e, const BwdArgs& p, int copy, int lane, bool detect,
+                                               bool& agg)
+{
+    int bin[4], bF, bL;
+    float4 o;
+    if (!agg) {
+        float ca, cb;
+        o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
+        bwd_scatter(accA, accB, bin[0], ca, cb, p.lanes, copy);
+        o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
+        bwd_scatter(accA, accB, bin[1], ca, cb, p.lanes, copy);
+        o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
+        bwd_scatter(accA, accB, bin[2], ca, cb, p.lanes, copy);
+        o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
+        bwd_scatter(accA, accB, bin[3], ca, cb, p.lanes, copy);
+        if (detect) {
+            const int b0 = __shfl_sync(0xffffffffu, bin[0], 0);
+            agg = __all_sync(0xffffffffu, bin[0] >= 0 && bin[0] == b0);
+        }
+        return o;
+    }
+    float ca[4], cb[4];
+    o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca[0], cb[0]);
+    o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca[1], cb[1]);
+    o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca[2], cb[2]);
+    o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca[3], cb[3]);
+    agg = warp_two_bins(bin, bF, bL);
+    if (agg) {
+        float aF = 0.0f, bFs = 0.0f, aL = 0.0f, bLs = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool f = bin[k] == bF;
+            aF += f ? ca[k] : 0.0f;
+            bFs += f ? cb[k] : 0.0f;
+            aL += f ? 0.0f : ca[k];
+            bLs += f ? 0.0f : cb[k];
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            aF += __shfl_xor_sync(0xffffffffu, aF, o2);
+            bFs += __shfl_xor_sync(0xffffffffu, bFs, o2);
+            aL += __shfl_xor_sync(0xffffffffu, aL, o2);
+            bLs += __shfl_xor_sync(0xffffffffu, bLs, o2);
+        }
+        if (lane == 0) {
+            atomicAdd(accA + bF * p.lanes, aF);
+            atomicAdd(accB + bF * p.lanes, bFs);
+        } else if (lane == 1 && bL != bF) {
+            const int c1 = 1 & (p.lanes - 1);
+            atomicAdd(accA + bL * p.lanes + c1, aL);
+            atomicAdd(accB + bL * p.lanes + c1, bLs);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) bwd_scatter(accA, accB, bin[k], ca[k], cb[k], p.lanes, copy);
+    }
+    return o;
+}
+
 template <bool CHAINS>
 __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __restrict__ srec,
                                               const float* __restrict__ s_ih, float* accA, float* accB,
@@ -110,12 +220,16 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
 {
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int copy = threadIdx.x & (p.lanes - 1);
     const float4* xv = reinterpret_cast<const float4*>(x);
     const float4* gv = reinterpret_cast<const float4*>(gy);
     float4* ov = reinterpret_cast<float4*>(gx);
     int64_t i = tid;
-    for (; i + (kBwdUnroll - 1) * nthr < p.nvec; i += kBwdUnroll * nthr) {
+    bool agg = true;
+    // warp-uniform bound (the warp's last lane decides), so that the whole
+    // warp runs these iterations and their votes together
+    for (; i + (31 - lane) + (kBwdUnroll - 1) * nthr < p.nvec; i += kBwdUnroll * nthr) {
         float4 xs[kBwdUnroll], gs[kBwdUnroll];
 #pragma unroll
         for (int u = 0; u < kBwdUnroll; ++u) {
@@ -123,14 +237,9 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
             gs[u] = __ldcs(gv + i + u * nthr);
         }
 #pragma unroll
-        for (int u = 0; u < kBwdUnroll; ++u) {
-            float4 o;
-            o.x = bwd_one<CHAINS>(xs[u].x, gs[u].x, srec, s_ih, accA, accB, e, p, copy);
-            o.y = bwd_one<CHAINS>(xs[u].y, gs[u].y, srec, s_ih, accA, accB, e, p, copy);
-            o.z = bwd_one<CHAINS>(xs[u].z, gs[u].z, srec, s_ih, accA, accB, e, p, copy);
-            o.w = bwd_one<CHAINS>(xs[u].w, gs[u].w, srec, s_ih, accA, accB, e, p, copy);
-            __stcs(ov + i + u * nthr, o);
-        }
+        for (int u = 0; u < kBwdUnroll; ++u)
+            __stcs(ov + i + u * nthr, bwd_vec_warp<CHAINS>(xs[u], gs[u], srec, s_ih, accA, accB, e, p, copy, lane,
+                                                               u == kBwdUnroll - 1, agg));
     }
     for (; i < p.nvec; i += nthr) {
         const float4 xs = __ldcs(xv + i), gs = __ldcs(gv + i);
@@ -192,24 +301,60 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     }
 }
 
-// g_v[j] += A_{j+1} + B_j (+ clamped terms), g_x[j] += -s_{j+1} A_{j+1} - s_j B_j
-__global__ void backward_reduce_kernel(const float* __restrict__ partials, int rows, int N,
-                                       const float* __restrict__ slope, float* g_values, float* g_knots)
+// g_v[j] += A_{j+1} + B_j (+ clamped terms), g_x[j] += -s_{j+1} A_{j+1} - s_j B_j.
+// A CTA covers kRedKnots consecutive knots; its kRedGroups warps-worth of
+// threads split the partial-sum rows (thread group g takes rows g, g + G, ...;
+// coalesced 128-byte reads per row), and group 0 adds the groups' FP64 sums
+// in a fixed order, so the result does not depend on scheduling.  Column j+1
+// of a row is A_{j+1} (j = N: the right-clamped sum), column N+2+j is B_j
+// (j = 0: column 0, the left-clamped sum), so g_v[j] is always the sum of
+// the two columns.
+constexpr int kRedKnots = 32, kRedGroups = 16;
+
+__global__ void __launch_bounds__(kRedKnots * kRedGroups)
+    backward_reduce_kernel(const float* __restrict__ partials, int rows, int N, const float* __restrict__ slope,
+                           float* g_values, float* g_knots)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > N) return;
-    const int W = 2 * (N + 2);
-    double Aj1 = 0.0, Bj = 0.0, clamped = 0.0;
-    for (int r = 0; r < rows; ++r) {
-        const float* row = partials + (size_t)r * W;
-        if (j < N) Aj1 += (double)row[j + 1];
-        if (j > 0) Bj += (double)row[N + 2 + j];
-        if (j == 0) clamped += (double)row[0];
-        if (j == N) clamped += (double)row[N + 1];
+    __shared__ double s_a[kRedGroups][kRedKnots], s_b[kRedGroups][kRedKnots];
+    const int lane = threadIdx.x % kRedKnots, grp = threadIdx.x / kRedKnots;
+    const int j = blockIdx.x * kRedKnots + lane;
+    const size_t W = 2 * (size_t)(N + 2);
+    double a = 0.0, b = 0.0;
+    if (j <= N) {
+        const float* colA = partials + (j + 1);
+        const float* colB = partials + (j == 0 ? 0 : N + 2 + j);
+        int r = grp;
+        for (; r + 3 * kRedGroups < rows; r += 4 * kRedGroups) {
+            float va[4], vb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                va[u] = __ldg(colA + (size_t)(r + u * kRedGroups) * W);
+                vb[u] = __ldg(colB + (size_t)(r + u * kRedGroups) * W);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a += (double)va[u];
+                b += (double)vb[u];
+            }
+        }
+        for (; r < rows; r += kRedGroups) {
+            a += (double)__ldg(colA + (size_t)r * W);
+            b += (double)__ldg(colB + (size_t)r * W);
+        }
     }
-    if (g_values) g_values[j] += (float)(Aj1 + Bj + clamped);
+    s_a[grp][lane] = a;
+    s_b[grp][lane] = b;
+    __syncthreads();
+    if (grp != 0 || j > N) return;
+    for (int g = 1; g < kRedGroups; ++g) {
+        a += s_a[g][lane];
+        b += s_b[g][lane];
+    }
+    if (g_values) g_values[j] += (float)(a + b);
     if (g_knots) {
-        const double gk = -(double)slope[j + 1] * Aj1 - (double)slope[j] * Bj;
+        double gk = 0.0;
+        if (j < N) gk -= (double)slope[j + 1] * a;
+        if (j > 0) gk -= (double)slope[j] * b;
         g_knots[j] += (float)gk;
     }
 }
@@ -257,8 +402,8 @@ pwl_status backward_launch(pwl_table t, const float* x, const float* gy, float* 
     backward_kernel<<<grid, sh.threads, sh.smem, s>>>(p, x, gy, gx, m, partials);
     PWL_CHECK_LAUNCH("backward_kernel");
     if (g_values || g_knots) {
-        backward_reduce_kernel<<<(int)((t->N + 1 + 255) / 256), 256, 0, s>>>(partials, grid, (int)t->N,
-                                                                          t->slope, g_values, g_knots);
+        backward_reduce_kernel<<<(int)((t->N + kRedKnots) / kRedKnots), kRedKnots * kRedGroups, 0, s>>>(
+            partials, grid, (int)t->N, t->slope, g_values, g_knots);
         PWL_CHECK_LAUNCH("backward_reduce_kernel");
     }
     return PWL_OK;

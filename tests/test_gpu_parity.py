@@ -266,6 +266,46 @@ def test_backward_matches_oracle(pwl, workloads, name, N):
     t.close()
 
 
+def _sorted_and_clustered_sets(xk, m, g):
+    """Query sets whose warps fall in one or two intervals (the warp-aggregated
+    scatter) next to warps that do not: sorted uniform queries, one interval,
+    two adjacent intervals in sorted blocks, and sorted queries with clamped
+    and out-of-domain ones sprinkled in."""
+    a, b = float(xk[0]), float(xk[-1])
+    k = len(xk) // 2
+    x0, x1, x2 = float(xk[k - 1]), float(xk[k]), float(xk[k + 1])
+    u = torch.rand(m, generator=g, dtype=torch.float64, device="cuda")
+    sets = {
+        "sorted": torch.sort((a + (b - a) * u).float()).values,
+        "one_interval": (x1 + (x2 - x1) * 0.999 * u).float(),
+        "two_intervals": torch.sort((x0 + (x2 - x0) * 0.999 * u).float()).values,
+    }
+    mixed = sets["sorted"].clone()
+    idx = torch.randint(0, m, (m // 500,), generator=g, device="cuda")
+    mixed[idx] = torch.tensor([a - 1.0, b + 1.0, a, b], device="cuda").repeat(len(idx) // 4 + 1)[:len(idx)]
+    sets["sorted_with_ends"] = mixed
+    return sets
+
+
+@pytest.mark.parametrize("N", [256, 4096])
+def test_backward_sorted_and_clustered_queries(pwl, workloads, N):
+    f = workloads.GAUSSIAN
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 20) + 13
+    g = torch.Generator(device="cuda").manual_seed(21)
+    gy = workloads.upstream_grad((m,), seed=5)
+    gys = gy.cpu().numpy().astype(np.float64)
+    for name, x in _sorted_and_clustered_sets(xk, m, g).items():
+        gv = torch.zeros(N + 1, device="cuda")
+        gk = torch.zeros(N + 1, device="cuda")
+        gx = t.backward(x, gy, None, gv, gk)
+        rgx, rgv, rgk, rgva, rgka = oracle.evaluate_grad(xk, vk, x.cpu().numpy().astype(np.float64), gys)
+        assert np.abs(gx.cpu().numpy() - rgx).max() <= EVAL_REL * np.abs(rgx).max(), name
+        assert np.all(np.abs(gv.cpu().numpy() - rgv) <= GRAD_REL * rgva + 1e-30), name
+        assert np.all(np.abs(gk.cpu().numpy() - rgk) <= GRAD_REL * rgka + 1e-30), name
+    t.close()
+
+
 def test_invalid_arguments_are_rejected(pwl, workloads):
     from paper_1510_02975_gb300 import PwlError
     bad = dict(workloads.GAUSSIAN, a=1.0, b=0.0)
