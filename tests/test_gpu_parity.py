@@ -291,7 +291,9 @@ def _sorted_and_clustered_sets(xk, m, g):
 def test_backward_sorted_and_clustered_queries(pwl, workloads, N):
     f = workloads.GAUSSIAN
     t, xk, vk = _table_and_ref(pwl, f, N)
-    m = (1 << 20) + 13
+    # ~7 vectors per thread: warps switch between the per-lane and the
+    # aggregated scatter several times
+    m = (1 << 22) + 13
     g = torch.Generator(device="cuda").manual_seed(21)
     gy = workloads.upstream_grad((m,), seed=5)
     gys = gy.cpu().numpy().astype(np.float64)
