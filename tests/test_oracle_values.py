@@ -147,6 +147,9 @@ def test_projection_matches_dense_least_squares(desc, N):
     assert np.abs(c - ref).max() < 2e-6 * scale
 
 
+# quad may report that it cannot certify its 1e-14 absolute tolerance on the
+# J0 products; the assertion below bounds the integral itself
+@pytest.mark.filterwarnings("ignore::scipy.integrate.IntegrationWarning")
 @pytest.mark.parametrize("desc", [GAUSS, LOR, J0], ids=lambda d: d["kind"])
 def test_projection_residual_is_orthogonal(desc):
     # <f - P_T f, phi_j> = 0 (Eq. 5), the integral by scipy's quadrature
