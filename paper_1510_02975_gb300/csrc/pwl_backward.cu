@@ -42,6 +42,7 @@ struct BwdArgs {
     const float* slope;
     int N, K, n_smem, max_chain;
     int lanes;          // accumulator copies (1, 8 or 32), lane l adds into copy l mod lanes
+    int rep_shift;      // log2 of the record copies R: lane l reads srec[c R + l mod R]
     float a, b, inv_w, off;
     float s_first, s_last;  // slopes of intervals 1 and N (set by the kernel)
     int64_t nvec;       // float4 vectors (x, gy and gx all 16-byte aligned), else 0
@@ -67,11 +68,11 @@ __device__ __forceinline__ float bwd_query(float x, float g, const float4* __res
 {
     const float xc = fminf(fmaxf(x, p.a), p.b);  // NaN -> a
     const int c = cell_of(xc, p.inv_w, p.off, p.K);
-    float4 r = (c < p.n_smem) ? srec[c] : __ldg(p.rec + c);
+    float4 r = (c < p.n_smem) ? srec[c << p.rep_shift] : __ldg(p.rec + c);
     if (CHAINS) {
         for (int it = 0; it < p.max_chain && xc >= r.x && is_link(r.w); ++it) {
             const int j = link_index(r.w);
-            r = (j < p.n_smem) ? srec[j] : __ldg(p.rec + j);
+            r = (j < p.n_smem) ? srec[j << p.rep_shift] : __ldg(p.rec + j);
         }
     }
     const uint32_t jy = __float_as_uint(r.y);
@@ -87,20 +88,22 @@ __device__ __forceinline__ float bwd_query(float x, float g, const float4* __res
     const float tt = (lside ? (r.x - xc) : (xc - r.x)) * ih;
     const float delta = lside ? 1.0f - tt : tt;
     const float one_minus = lside ? tt : 1.0f - tt;
-    const bool interior = x > p.a && x < p.b;  // false for NaN
-    bin = interior ? i : -1;
+    bin = i;
     ca = g * one_minus;
     cb = g * delta;
-    // the ends: clamped queries feed g_v[0] or g_v[N]; x = a is interval 1 at
-    // delta = 0, x = b interval N at delta = 1
-    e.clamped_left += x < p.a ? g : 0.0f;
-    e.at_a += x == p.a ? g : 0.0f;
-    e.clamped_right += x > p.b ? g : 0.0f;
-    e.at_b += x == p.b ? g : 0.0f;
-    float gx = interior ? g * s : 0.0f;
-    gx = x == p.a ? g * p.s_first : gx;
-    gx = x == p.b ? g * p.s_last : gx;
-    return x != x ? x : gx;
+    float gx = g * s;
+    if (!(x > p.a && x < p.b)) {  // the ends, beyond them, NaN: rare in most query sets
+        bin = -1;
+        // clamped queries feed g_v[0] or g_v[N]; x = a is interval 1 at
+        // delta = 0, x = b interval N at delta = 1
+        e.clamped_left += x < p.a ? g : 0.0f;
+        e.at_a += x == p.a ? g : 0.0f;
+        e.clamped_right += x > p.b ? g : 0.0f;
+        e.at_b += x == p.b ? g : 0.0f;
+        gx = x == p.a ? g * p.s_first : (x == p.b ? g * p.s_last : 0.0f);
+        gx = x != x ? x : gx;
+    }
+    return gx;
 }
 
 // A query's two sums into its lane's accumulator copy (one predicated pair
@@ -258,8 +261,10 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
                                                         float* gx, int64_t m, float* partials)
 {
     extern __shared__ float4 s_dyn[];
-    float4* srec = s_dyn;
-    float* s_ih = reinterpret_cast<float*>(s_dyn + args.n_smem);
+    const int R = 1 << args.rep_shift;
+    // this lane's record copy: srec[c << rep_shift] is copy (lane mod R) of record c
+    const float4* srec = s_dyn + (threadIdx.x & (R - 1));
+    float* s_ih = reinterpret_cast<float*>(s_dyn + (size_t)args.n_smem * R);
     float* accA = s_ih + (args.N + 2);
     float* accB = accA + (size_t)(args.N + 2) * args.lanes;
     BwdArgs p = args;
@@ -268,7 +273,8 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     p.n_smem = min(p.K + n_chain, p.n_smem);
     p.s_first = p.slope[1];
     p.s_last = p.slope[p.N];
-    for (int i = threadIdx.x; i < p.n_smem; i += blockDim.x) srec[i] = __ldg(p.rec + i);
+    for (int i = threadIdx.x; i < (p.n_smem << p.rep_shift); i += blockDim.x)
+        s_dyn[i] = __ldg(p.rec + (i >> p.rep_shift));
     for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) s_ih[i] = p.inv_h[i];
     for (int i = threadIdx.x; i < 2 * (p.N + 2) * p.lanes; i += blockDim.x) accA[i] = 0.0f;
     __syncthreads();
@@ -392,6 +398,8 @@ pwl_status backward_launch(pwl_table t, const float* x, const float* gy, float* 
     p.n_smem = (int)sh.n_smem;
     p.max_chain = 0;
     p.lanes = backward_lanes(t);
+    p.rep_shift = 0;
+    while ((1 << p.rep_shift) < backward_record_copies(t)) ++p.rep_shift;
     p.a = t->a;
     p.b = t->b;
     p.inv_w = t->inv_w_b;

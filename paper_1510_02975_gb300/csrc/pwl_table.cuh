@@ -51,18 +51,33 @@ inline size_t backward_fixed_smem(const pwl_table_s* t)
 {
     return (4 + 8 * (size_t)backward_lanes(t)) * (size_t)(t->N + 2);
 }
+// Record copies R (1, 2, 4 or 8; the largest that fits next to the
+// accumulators with every record staged).  A warp's 16-byte gathers are served
+// a quarter warp (8 lanes) at a time, and 8 random records of one copy
+// collide in ~2.5 of the 8 16-byte bank groups; copy g of record c sits at
+// index c R + g and lane l reads copy l mod R, so with R = 8 the lanes of a
+// quarter warp always hit 8 different bank groups.
+inline int backward_record_copies(const pwl_table_s* t)
+{
+    const size_t optin = device_info().smem_optin;
+    const size_t fixed = backward_fixed_smem(t);
+    const size_t rec = 16 * (size_t)(t->Kb + t->chain_reserve_b);
+    for (int R = 8; R > 1; R /= 2)
+        if (fixed + rec * (size_t)R <= optin) return R;
+    return 1;
+}
 inline int64_t backward_smem_records(const pwl_table_s* t)
 {
     const size_t optin = device_info().smem_optin;
     const size_t fixed = backward_fixed_smem(t);
     if (fixed + 16 * 64 > optin) return -1;  // does not fit: unsupported
-    const int64_t cap = (int64_t)((optin - fixed) / sizeof(float4));
+    const int64_t cap = (int64_t)((optin - fixed) / (sizeof(float4) * (size_t)backward_record_copies(t)));
     return std::min<int64_t>(t->Kb + t->chain_reserve_b, cap);
 }
 inline size_t backward_smem_bytes(const pwl_table_s* t)
 {
     const int64_t r = backward_smem_records(t);
-    return r < 0 ? 0 : sizeof(float4) * (size_t)r + backward_fixed_smem(t);
+    return r < 0 ? 0 : sizeof(float4) * (size_t)r * (size_t)backward_record_copies(t) + backward_fixed_smem(t);
 }
 
 // Persistent grid of a kernel: resident CTAs per SM (registers, shared
