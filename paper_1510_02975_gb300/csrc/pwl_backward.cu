@@ -144,38 +144,94 @@ __device__ __forceinline__ bool warp_two_bins(const int (&bin)[4], int& bF, int&
     return __all_sync(0xffffffffu, ok);
 }
 
+// A warp's hot interval (warp-uniform; -1: none) and this lane's sums A, B
+// for it, kept in registers instead of shared-memory atomics.
+struct HotBin {
+    int bin;
+    float a, b;
+};
+
+// lanes (of 32) that must share lane 0's interval on a detection vote for the
+// interval to become the warp's hot one
+constexpr int kHotLanes = 8;
+
+// The hot interval's sums into shared memory (warp-uniform call: every lane
+// of the warp runs it)
+__device__ __forceinline__ void flush_hot(float* accA, float* accB, HotBin& h, int lanes, int lane)
+{
+    if (h.bin < 0) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        h.a += __shfl_xor_sync(0xffffffffu, h.a, o);
+        h.b += __shfl_xor_sync(0xffffffffu, h.b, o);
+    }
+    if (lane == 0) {
+        atomicAdd(accA + h.bin * lanes, h.a);
+        atomicAdd(accB + h.bin * lanes, h.b);
+    }
+    h.a = 0.0f;
+    h.b = 0.0f;
+}
+
+// A query's sums: into the hot interval's registers, or the lane's copy
+__device__ __forceinline__ void bwd_scatter_hot(float* accA, float* accB, int bin, float ca, float cb, int lanes,
+                                                int copy, HotBin& h)
+{
+    const bool hit = bin == h.bin;
+    h.a += hit ? ca : 0.0f;
+    h.b += hit ? cb : 0.0f;
+    bwd_scatter(accA, accB, hit ? -1 : bin, ca, cb, lanes, copy);
+}
+
 // Four consecutive queries per lane, 128 per warp, all 32 lanes active.
 // Warp-aggregated scatter-add for sorted or clustered queries, where per-lane
 // atomics would all hit one or two addresses and serialise: when the whole
 // vector lies in intervals bF and bL, the warp sums the two intervals' A and
 // B by shuffles and lanes 0 and 1 add them with four atomics.  A warp runs in
 // one of two modes (`agg`, warp-uniform).  Per lane: each query's atomics
-// are issued right after its lookup, and on `detect` vectors a single vote
-// (is every lane's first query interior and in the warp's first interval?)
-// switches to the aggregated mode.  Aggregated: the vector's lookups come
-// first, and a vector that spans more intervals falls back to per-lane
-// atomics and switches back.
+// are issued right after its lookup, and on `detect` vectors one ballot on
+// the lanes' first queries against lane 0's interval decides: all 32 lanes
+// in it switch to the aggregated mode; kHotLanes or more make it the warp's
+// hot interval (a point mass scattered through the stream, which no vector
+// aggregates: its queries' sums then stay in registers).  Aggregated: the
+// vector's lookups come first, and a vector that spans more intervals falls
+// back to per-lane atomics and switches back.
 template <bool CHAINS>
 __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float4* __restrict__ srec,
                                                const float* __restrict__ s_ih, float* accA, float* accB,
                                                EndSums& e, const BwdArgs& p, int copy, int lane, bool detect,
-                                               bool& agg)
+                                               bool& agg, HotBin& hot)
 {
     int bin[4], bF, bL;
     float4 o;
     if (!agg) {
         float ca, cb;
-        o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
-        bwd_scatter(accA, accB, bin[0], ca, cb, p.lanes, copy);
-        o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
-        bwd_scatter(accA, accB, bin[1], ca, cb, p.lanes, copy);
-        o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
-        bwd_scatter(accA, accB, bin[2], ca, cb, p.lanes, copy);
-        o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
-        bwd_scatter(accA, accB, bin[3], ca, cb, p.lanes, copy);
+        if (hot.bin < 0) {
+            o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
+            bwd_scatter(accA, accB, bin[0], ca, cb, p.lanes, copy);
+            o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
+            bwd_scatter(accA, accB, bin[1], ca, cb, p.lanes, copy);
+            o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
+            bwd_scatter(accA, accB, bin[2], ca, cb, p.lanes, copy);
+            o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
+            bwd_scatter(accA, accB, bin[3], ca, cb, p.lanes, copy);
+        } else {
+            o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
+            bwd_scatter_hot(accA, accB, bin[0], ca, cb, p.lanes, copy, hot);
+            o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
+            bwd_scatter_hot(accA, accB, bin[1], ca, cb, p.lanes, copy, hot);
+            o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
+            bwd_scatter_hot(accA, accB, bin[2], ca, cb, p.lanes, copy, hot);
+            o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
+            bwd_scatter_hot(accA, accB, bin[3], ca, cb, p.lanes, copy, hot);
+        }
         if (detect) {
             const int b0 = __shfl_sync(0xffffffffu, bin[0], 0);
-            agg = __all_sync(0xffffffffu, bin[0] >= 0 && bin[0] == b0);
+            const unsigned same = __ballot_sync(0xffffffffu, bin[0] >= 0 && bin[0] == b0);
+            agg = same == 0xffffffffu;
+            if (!agg && b0 != hot.bin && __popc(same) >= kHotLanes) {
+                flush_hot(accA, accB, hot, p.lanes, lane);
+                hot.bin = b0;
+            }
         }
         return o;
     }
@@ -230,6 +286,7 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
     float4* ov = reinterpret_cast<float4*>(gx);
     int64_t i = tid;
     bool agg = true;
+    HotBin hot{-1, 0.0f, 0.0f};
     // warp-uniform bound (the warp's last lane decides), so that the whole
     // warp runs these iterations and their votes together
     for (; i + (31 - lane) + (kBwdUnroll - 1) * nthr < p.nvec; i += kBwdUnroll * nthr) {
@@ -242,7 +299,7 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
 #pragma unroll
         for (int u = 0; u < kBwdUnroll; ++u)
             __stcs(ov + i + u * nthr, bwd_vec_warp<CHAINS>(xs[u], gs[u], srec, s_ih, accA, accB, e, p, copy, lane,
-                                                               u == kBwdUnroll - 1, agg));
+                                                               u == kBwdUnroll - 1, agg, hot));
     }
     for (; i < p.nvec; i += nthr) {
         const float4 xs = __ldcs(xv + i), gs = __ldcs(gv + i);
@@ -255,6 +312,7 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
     }
     for (int64_t q = p.nvec * 4 + tid; q < m; q += nthr)
         gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, e, p, copy);
+    flush_hot(accA, accB, hot, p.lanes, lane);  // every lane of the warp gets here
 }
 
 __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, const float* x, const float* gy,

@@ -269,8 +269,9 @@ def test_backward_matches_oracle(pwl, workloads, name, N):
 def _sorted_and_clustered_sets(xk, m, g):
     """Query sets whose warps fall in one or two intervals (the warp-aggregated
     scatter) next to warps that do not: sorted uniform queries, one interval,
-    two adjacent intervals in sorted blocks, and sorted queries with clamped
-    and out-of-domain ones sprinkled in."""
+    two adjacent intervals in sorted blocks, sorted queries with clamped and
+    out-of-domain ones sprinkled in, and random queries with a point mass
+    inside an interval or at a knot."""
     a, b = float(xk[0]), float(xk[-1])
     k = len(xk) // 2
     x0, x1, x2 = float(xk[k - 1]), float(xk[k]), float(xk[k + 1])
@@ -284,6 +285,15 @@ def _sorted_and_clustered_sets(xk, m, g):
     idx = torch.randint(0, m, (m // 500,), generator=g, device="cuda")
     mixed[idx] = torch.tensor([a - 1.0, b + 1.0, a, b], device="cuda").repeat(len(idx) // 4 + 1)[:len(idx)]
     sets["sorted_with_ends"] = mixed
+    # point masses scattered through a random stream (the hot-interval sums):
+    # half the queries inside one interval, and 30% exactly at a knot
+    u32 = (a + (b - a) * u).float()
+    pm = u32.clone()
+    pm[torch.rand(m, generator=g, device="cuda") < 0.5] = float(0.5 * (x1 + x2))
+    sets["point_mass"] = pm
+    pk = u32.clone()
+    pk[torch.rand(m, generator=g, device="cuda") < 0.3] = x1
+    sets["point_mass_at_knot"] = pk
     return sets
 
 
