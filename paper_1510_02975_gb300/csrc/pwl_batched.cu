@@ -318,6 +318,17 @@ __device__ __forceinline__ void run_staged(const EvalParams& p, const BatchFunc&
     run_piece<U, 0, true>(p, g, w, buf, x, y, nullptr);
 }
 
+// n float2 records from global memory into shared memory by the whole CTA,
+// as 8-byte cp.async copies that use no registers: every thread issues all
+// of its copies (~10 for an average index) before one wait, so staging a
+// function's index costs about one load latency instead of one per THREADS
+// records.  The caller commits, waits and synchronises.
+template <int THREADS>
+__device__ __forceinline__ void stage_records(float2* dst, const float2* __restrict__ src, int n)
+{
+    for (int i = threadIdx.x; i < n; i += THREADS) cp_async8(dst + i, src + i);
+}
+
 // Staging by the CTA's threads: the SM streams nothing while a CTA copies
 // (other CTAs on the SM, if any, keep streaming).  MODE 0: stage the pieces
 // the plan marks; MODE 1: no record staging, every piece reads its records
@@ -340,11 +351,10 @@ __global__ void __launch_bounds__(THREADS, MINB) batch_eval_kernel(const EvalPar
         if (MODE == 0 && w.staged) {
             if (staged_f != w.f) {
                 __syncthreads();  // nobody reads the previous function's records any more
-                const float2* P = p.recP + g.poff;
-                const float2* S = p.recS + 2 * g.koff;
-                const int K = g.K, nS = 2 * (g.N + 1);
-                for (int i = threadIdx.x; i < K; i += THREADS) s_idx[i] = __ldg(P + i);
-                for (int i = threadIdx.x; i < nS; i += THREADS) s_idx[K + i] = __ldg(S + i);
+                stage_records<THREADS>(s_idx, p.recP + g.poff, g.K);
+                stage_records<THREADS>(s_idx + g.K, p.recS + 2 * g.koff, 2 * (g.N + 1));
+                cp_async_commit();
+                cp_async_wait<0>();
                 __syncthreads();
                 staged_f = w.f;
             }
