@@ -89,7 +89,7 @@ __device__ __forceinline__ double density_chunk(const pwl_func& F, int64_t c0, i
             // t_k = a + (k + 1/2) delta, rounded as written (no fused multiply-add)
             const double t = __dadd_rn(F.a, __dmul_rn((double)k + 0.5, delta));
             const T f2 = func_second_derivative_k<SAMPLED, T>(F, (T)t);
-            const double dk = (double)FMath<T>::pw(fabs(f2), T(0.4));
+            const double dk = (double)FMath<T>::dens(f2);
             d[k] = dk;
             acc += dk;
         }
@@ -263,7 +263,7 @@ template <bool SAMPLED>
 __device__ __forceinline__ double fused_density64(const pwl_func& F, double a, double delta, int64_t k)
 {
     const double t = __dadd_rn(a, __dmul_rn((double)k + 0.5, delta));
-    return pow(fabs(func_second_derivative_k<SAMPLED, double>(F, t)), 0.4);
+    return pow_two_fifths(func_second_derivative_k<SAMPLED, double>(F, t));
 }
 
 // The densities of one chunk's cells of this thread, added to `part`; STORE

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kConstThreads) error_constants_kernel(pwl_func
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M; k += stride) {
         const double t = __dadd_rn(F.a, __dmul_rn((double)k + 0.5, delta));
         const double f2 = func_second_derivative_k<SAMPLED, double>(F, t);
-        s25 += pow(fabs(f2), 0.4);
+        s25 += pow_two_fifths(f2);
         s2 = __fma_rn(f2, f2, s2);
     }
     for (int o = 16; o > 0; o >>= 1) {
