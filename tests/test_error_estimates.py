@@ -92,6 +92,10 @@ def test_prediction_matches_oracle_error_on_optimised_partition(pwl, name, a, b,
     {"kind": "gaussian", "a": -4.0, "b": 4.0, "p": [1.0, 0.0, 1.0]},
     {"kind": "lorentzian", "a": -10.0, "b": 10.0, "p": [1.0, 0.0, 1.0]},
     {"kind": "bessel_j0", "a": 0.0, "b": 50.0, "p": [1.0, 3.0]},
+    # f'' = 9 e^{3 x} spans 3e-10 .. 2e11: the GPU's |f''|^{2/5} (an
+    # inverse-fifth-root iteration) against the oracle's C library pow (the
+    # midpoint rule on f''^2 stays within 6e-9 of the quadrature here)
+    {"kind": "exp", "a": -8.0, "b": 8.0, "p": [1.0, 3.0]},
 ])
 def test_error_constants_match_oracle(pwl, desc):
     M = 1 << 18
