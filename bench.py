@@ -736,7 +736,54 @@ def run_variants(args):
                                "N_uniform": n_uni, "uniform_over_optimised": round(n_uni / n_opt, 3)})
     peak, kind = measured_peaks()
     print(json.dumps({"report": "variants", "queries_per_launch": m, "peak_gbs": peak, "peak_kind": kind,
-                      "throughput": rows, "errors": errors, "n_for_error": sizing}), flush=True)
+                      "throughput": rows, "errors": errors, "n_for_error": sizing,
+                      "uniform_vs_optimised": uniform_vs_optimised(pwl, W, m, y, sizing)}), flush=True)
+
+
+def uniform_vs_optimised(pwl, W, m, y, sizing):
+    """The uniform partition's fast path against the nearly optimal partition
+    at equal predicted L2 error (Results 4-6): each table built at the N that
+    pwl_n_for_error gives for it; the uniform one with two cells per interval,
+    which pwl_eval serves from the 16-byte index (a cell holds at most one
+    knot: one record load, a compare and an FMA per query, the direct lookup
+    of Section IV made exact at the knots).  Throughput on uniform queries, the index's shared memory,
+    and the measured L2 error (midpoint sums of (y - f)^2 on 2^20 points, f in
+    FP64 by numpy / scipy) and max error against FP64 f."""
+    import torch
+    out = []
+    for row in sizing:
+        if row["target_l2"] not in (1e-4, 1e-6):
+            continue
+        name, form = row["func"], row["form"]
+        f = W.PAPER_FUNCTIONS[name]
+        a, b = f["a"], f["b"]
+        x = W.uniform_queries(f, m, seed=1)
+        n_pts = 1 << 20
+        xm = torch.tensor(a + (b - a) * (np.arange(n_pts) + 0.5) / n_pts, dtype=torch.float32, device="cuda")
+        xh = xm.cpu().numpy().astype(np.float64)
+        fx = f64(name, xh)
+        entry = {"func": name, "form": form, "target_l2": row["target_l2"]}
+        for label, n in (("optimised", row["N_optimised"]), ("uniform", row["N_uniform"])):
+            if label == "optimised":
+                kn = pwl.pwl_design(f, n)
+                t = pwl.Table(kn, pwl.pwl_project(f, kn, form))
+            else:
+                kn = a + (b - a) * torch.arange(n + 1, dtype=torch.float64, device="cuda") / n
+                kn[-1] = b
+                # two cells per interval: a knot sits on a cell boundary, and
+                # whichever way FP32 rounding moves it, no cell gets two
+                t = pwl.Table(kn, pwl.pwl_project(f, kn, form), "fp32", 2 * n)
+            sec = time_launches(lambda: pwl.pwl_eval(t.handle, x, y))
+            d = pwl.pwl_eval(t.handle, xm).cpu().numpy().astype(np.float64) - fx
+            entry[label] = {"N": n, "gbs": round(BYTES_FWD * m / sec / 1e9, 1),
+                            "layout": int(t.info["layout"]), "k_cells": int(t.info["k_cells"]),
+                            "n_chain": int(t.info["n_chain"]),
+                            "index_kb": round(t.info["eval_smem_bytes"] / 1024, 1),
+                            "l2_err": float(np.sqrt(np.sum(d * d) * (b - a) / n_pts)),
+                            "max_err": float(np.abs(d).max())}
+            t.close()
+        out.append(entry)
+    return out
 
 
 def run_channels(args):
