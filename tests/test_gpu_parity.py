@@ -318,6 +318,25 @@ def test_backward_sorted_and_clustered_queries(pwl, workloads, N):
     t.close()
 
 
+@pytest.mark.parametrize("name", FUNCS)
+@pytest.mark.parametrize("N", [7, 260, 2596])
+def test_uniform_partition_table(pwl, workloads, name, N):
+    # the uniform partition's lookup: two cells per interval put at most one
+    # knot in a cell whichever way FP32 rounds it, and pwl_eval serves the
+    # table from the 16-byte index without chains
+    f = workloads.PAPER_FUNCTIONS[name]
+    a, b = f["a"], f["b"]
+    kn = a + (b - a) * torch.arange(N + 1, dtype=torch.float64, device="cuda") / N
+    kn[-1] = b
+    vals = pwl.pwl_project(f, kn, "project")
+    t = pwl.Table(kn, vals, "fp32", 2 * N)
+    assert int(t.info["layout"]) == 1 and int(t.info["n_chain"]) == 0
+    x = workloads.uniform_queries(f, (1 << 20) + 3, seed=1)
+    x[: N + 1] = torch.tensor(round_knots(kn.cpu().numpy()), dtype=torch.float32, device="cuda")
+    _check_eval(t(x), round_knots(kn.cpu().numpy()), round_values(vals.cpu().numpy(), "fp32"), x)
+    t.close()
+
+
 def test_invalid_arguments_are_rejected(pwl, workloads):
     from paper_1510_02975_gb300 import PwlError
     bad = dict(workloads.GAUSSIAN, a=1.0, b=0.0)
