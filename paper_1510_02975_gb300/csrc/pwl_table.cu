@@ -291,8 +291,13 @@ void choose_cells(pwl_table t, float hmin, int64_t requested)
     const double need = ceil(((double)t->b - (double)t->a) / (double)hmin) + 1.0;
     // 8-byte index: worth its second, dependent gather on knot cells only
     // when it lets two CTAs share an SM while most cells (>= 3/4) are
-    // knot-free; otherwise the 16-byte index serves the forward path too
-    const size_t half = di.smem_per_sm / 2 - 1024;
+    // knot-free and no cell holds two knots; otherwise the 16-byte index
+    // serves the forward path too.  Two CTAs keep to kTwoCtaIndexBytes each:
+    // beyond it the shared-memory carve-out of two CTAs leaves the L1 ~28 KB
+    // for the streaming loads in flight (measured: ~5.55 TB/s at 102-113 KB
+    // per CTA against ~6.5 TB/s at 86-96 KB, the same tables).
+    constexpr size_t kTwoCtaIndexBytes = 96 * 1024;
+    const size_t half = std::min<size_t>(di.smem_per_sm / 2 - 1024, kTwoCtaIndexBytes);
     const int64_t cap2 = forward_cell_capacity(N, half);
     const int64_t cap1 = forward_cell_capacity(N, di.smem_optin);
     const double want = std::max<double>(need, 8.0 * (double)(N + 1));
@@ -300,7 +305,7 @@ void choose_cells(pwl_table t, float hmin, int64_t requested)
     if (requested > 0) {
         K = std::min<int64_t>(requested, cap1);
         t->layout = (K <= cap2 && K >= 4 * (N + 1)) ? 0 : 1;
-    } else if (cap2 >= 4 * (N + 1)) {
+    } else if ((double)cap2 >= std::max<double>(need, 4.0 * (double)(N + 1))) {
         K = (int64_t)std::min<double>(want, (double)cap2);
         t->layout = 0;
     } else {
