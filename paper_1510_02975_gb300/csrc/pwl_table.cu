@@ -309,8 +309,20 @@ void choose_cells(pwl_table t, float hmin, int64_t requested)
         K = (int64_t)std::min<double>(want, (double)cap2);
         t->layout = 0;
     } else {
-        K = (int64_t)std::min<double>(want, (double)cap1);
-        t->layout = 1;
+        // one CTA per SM: the 8-byte index still wins while it stays chain-free
+        // with >= 3 cells per knot inside kOneCtaIndexBytes (the carve-out then
+        // leaves the L1 ~60 KB; at ~206 KB it drops to ~28 KB: Gaussian
+        // N = 4096, 6.2 TB/s at 190 KB against 5.35 TB/s at 206 KB and
+        // 5.95 TB/s on the 16-byte index)
+        constexpr size_t kOneCtaIndexBytes = 190 * 1024;
+        const int64_t cap1b = forward_cell_capacity(N, std::min<size_t>(di.smem_optin, kOneCtaIndexBytes));
+        if ((double)cap1b >= std::max<double>(need, 3.0 * (double)(N + 1))) {
+            K = (int64_t)std::min<double>(want, (double)cap1b);
+            t->layout = 0;
+        } else {
+            K = (int64_t)std::min<double>(want, (double)cap1);
+            t->layout = 1;
+        }
     }
     t->K = std::max<int64_t>(K, 1);
     const int64_t capb = backward_cell_capacity(N);
