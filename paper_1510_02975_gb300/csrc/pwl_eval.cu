@@ -51,7 +51,23 @@ struct EvalArgs {
 // 8-byte layout.  Branch-free apart from chains: every lane computes its
 // cell anchor, knot lanes additionally load their side record (a predicated
 // load), and one FMA finishes.
-template <bool CHAINS>
+// A cell holding several knots: from its first knot k (at xk) to the last
+// knot <= xc, reading the knots from global memory.  Called out of line
+// (one CTA per SM), so that the lookup of the (many) queries in cells
+// without a chain keeps the instruction schedule of a chain-free table.
+__device__ __noinline__ int2 walk_chain8(float xc, int k, float xk, const float* __restrict__ xkg, int max_chain,
+                                         int N)
+{
+    for (int g = 0; g < max_chain && k < N; ++g) {
+        const float xn = __ldg(xkg + k + 1);
+        if (!(xc >= xn)) break;
+        ++k;
+        xk = xn;
+    }
+    return make_int2(k, __float_as_int(xk));
+}
+
+template <bool CHAINS, bool OUTLINE = false>
 struct Lerp8 {
     const float2* sP;
     const float2* sS;
@@ -69,11 +85,17 @@ struct Lerp8 {
             int k = (int)(bits & kKnotTagMask);
             float xk = r.y;
             if (CHAINS && (bits & kKnotTagChain)) {
-                for (int g = 0; g < p.max_chain && k < p.N; ++g) {
-                    const float xn = __ldg(p.xk + k + 1);
-                    if (!(xc >= xn)) break;
-                    ++k;
-                    xk = xn;
+                if (OUTLINE) {
+                    const int2 w = walk_chain8(xc, k, xk, p.xk, p.max_chain, p.N);
+                    k = w.x;
+                    xk = __int_as_float(w.y);
+                } else {
+                    for (int g = 0; g < p.max_chain && k < p.N; ++g) {
+                        const float xn = __ldg(p.xk + k + 1);
+                        if (!(xc >= xn)) break;
+                        ++k;
+                        xk = xn;
+                    }
                 }
             }
             // x == x_k takes the right side: v_k + 0 * s is exactly v_k
@@ -216,10 +238,12 @@ __global__ void __launch_bounds__(1024, MINB) eval_kernel(const EvalArgs args, c
         if (p.s_staged)
             for (int i = threadIdx.x; i < 2 * (p.N + 1); i += blockDim.x) sS[i] = __ldg(p.recS + i);
         __syncthreads();
+        // the chain walk out of line where the registers allow the call (one
+        // CTA per SM); inline at two CTAs per SM (32 registers a thread)
         if (n_chain == 0)
             eval_body<IO, U>(p, Lerp8<false>{sP, sS, p}, x, y, m);
         else
-            eval_body<IO, U>(p, Lerp8<true>{sP, sS, p}, x, y, m);
+            eval_body<IO, U>(p, Lerp8<true, MINB == 1>{sP, sS, p}, x, y, m);
     } else {
         const int n_chain = p.hdr->n_chain_b;
         p.max_chain = p.hdr->max_chain_b;
