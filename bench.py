@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=21, help="oracle queries per (table, set)")
     ap.add_argument("--fwd-bwd-steps", type=int, default=3)
-    ap.add_argument("--report", default=None, choices=[None, "variants", "channels", "batched"],
+    ap.add_argument("--report", default=None, choices=[None, "variants", "channels", "batched", "backward"],
                     help="variants: per-table throughput of every evaluation path and the error of each "
                          "vertex-table precision (one JSON line)")
     ap.add_argument("--k-cells", type=int, default=0, help="cell count of the tables in --report variants")
@@ -786,6 +786,48 @@ def uniform_vs_optimised(pwl, W, m, y, sizing):
     return out
 
 
+def run_backward(args):
+    """pwl_eval_backward (x, values, knots) per call on the Gaussian tables at
+    N in {256, 1024, 4096} (P_T values), 2^log2m queries, for query sets that
+    take different scatter paths: uniform (per-lane atomics), sorted
+    (warp-aggregated), normal(0, 1.5) clipped to the domain, and uniform with
+    half the queries at x = 0 (the hot interval).  CUDA events over 10 calls
+    after one warm-up call, each call the backward and its row reduction."""
+    import torch
+
+    import paper_1510_02975_gb300 as pwl
+    from paper_1510_02975_gb300 import _build
+    from paper_1510_02975_gb300 import workloads as W
+    _build.build()
+    f = W.GAUSSIAN
+    m = 1 << args.log2m
+    xu = W.uniform_queries(f, m, seed=1)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    xp = xu.clone()
+    xp[torch.rand(m, generator=g, device="cuda") < 0.5] = 0.0
+    sets = {"uniform": xu, "sorted": torch.sort(xu).values, "normal_clipped": W.normal_queries(f, m, seed=2),
+            "half_at_zero": xp}
+    gy = W.upstream_grad((m,), seed=5)
+    gx = torch.empty_like(gy)
+    lib = pwl._capi.load()
+    out = []
+    for N in NS:
+        kn = pwl.pwl_design(f, N)
+        t = pwl.Table(kn, pwl.pwl_project(f, kn, "project"))
+        ws = torch.empty(lib.pwl_eval_backward_workspace_size(t.handle), dtype=torch.uint8, device="cuda")
+        gv = torch.zeros(N + 1, device="cuda")
+        gk = torch.zeros(N + 1, device="cuda")
+        row = {"N": N, "backward_smem_kb": round(t.info["backward_smem_bytes"] / 1024, 1)}
+        for name, x in sets.items():
+            sec = time_launches(lambda: pwl.pwl_eval_backward(t.handle, x, gy, gx, gv, gk, ws), reps=10)
+            row[name] = {"us": round(sec * 1e6, 1), "gbs": round(BYTES_BWD * m / sec / 1e9, 1)}
+        out.append(row)
+        t.close()
+    peak, kind = measured_peaks()
+    print(json.dumps({"report": "backward", "queries": m, "bytes_per_query": BYTES_BWD, "peak_gbs": peak,
+                      "peak_kind": kind, "tables": out}), flush=True)
+
+
 def run_channels(args):
     """Channel-wise learnable map: x[65536, 4096] ~ N(0, 2^2) (FP32 and BF16),
     4096 channels of 257 knots on [-8, 8] from the Gaussian design and P_T
@@ -965,6 +1007,9 @@ def main():
         return
     if args.report == "batched":
         run_batched(args)
+        return
+    if args.report == "backward":
+        run_backward(args)
         return
     if args.impl == "reference":
         run_reference(args)
