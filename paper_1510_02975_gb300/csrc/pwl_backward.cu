@@ -9,10 +9,14 @@
 //   g_v[j]  += A_{j+1} + B_j            g_x[j] += -s_{j+1} A_{j+1} - s_j B_j
 // (clamped queries add gy to g_v[0] or g_v[N] only).
 //
-// Pass 1 (persistent grid): every CTA stages the backward records and the
-// reciprocal lengths, streams (x, gy) -> gx with 16-byte vectors, and
-// accumulates A, B in shared memory with FP32 atomics; it then writes its
-// partial sums to the workspace (one row per CTA).
+// Pass 1 (persistent grid): every CTA stages the backward records (in up to
+// 8 bank-private copies) and the reciprocal lengths, streams (x, gy) -> gx
+// with 16-byte vectors, and accumulates A, B in shared memory: per-lane FP32
+// atomics into up to 32 accumulator copies for random queries, a warp-level
+// sum for vectors that lie in one or two intervals (sorted or clustered
+// queries), and registers for a warp's hot interval (a point mass) and for
+// the queries at or beyond the ends of [a, b].  It then writes its partial
+// sums to the workspace (one row per CTA).
 // Pass 2: 32 knots per CTA, the CTA rows split over 16 thread groups, sums
 // the rows in a fixed order (FP64) and forms g_v and g_x (the order of the
 // in-CTA atomics still varies from run to run, so the sums are reproducible
