@@ -217,14 +217,18 @@ pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_
 /* Rebuilds the table in place from new FP64 knots and values (same N, value
  * dtype and cell count), asynchronously on `stream` and without allocating:
  * the call a training or design loop makes every step.  The knots must stay
- * strictly increasing after rounding to FP32 and every value and slope
- * finite; this call does not check (pwl_table_check does).  It must not
- * overlap other work on the same table.                                     */
+ * strictly increasing after rounding to FP32, every value and slope finite,
+ * and the end knots x_0, x_N must round to the FP32 values of the build (the
+ * cell grids span the built [x_0, x_N]; interior knots may move freely).
+ * This call does not check; pwl_table_check reports a violation, after
+ * which evaluation is unspecified until a valid update.  The comparison
+ * path's texture (pwl_eval_variant mode 1), if created, is refreshed on
+ * `stream` too.  It must not overlap other work on the same table.          */
 pwl_status pwl_table_update(pwl_table t, const double* d_knots, const double* d_values, void* stream);
 
 /* Status of the last build or update: PWL_EINVAL if the rounded knots were
- * not strictly increasing or a value or slope not finite.  Synchronizes
- * `stream`.                                                                 */
+ * not strictly increasing, a value or slope not finite, or an update moved
+ * an end knot.  Synchronizes `stream`.                                      */
 pwl_status pwl_table_check(pwl_table t, void* stream);
 
 pwl_status pwl_table_destroy(pwl_table t);

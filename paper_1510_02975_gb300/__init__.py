@@ -507,19 +507,21 @@ def _autograd_classes():
 
     class _ChannelFn(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, x, knots, values, k_cells, k_cells_bwd):
+        def forward(ctx, x, knots, values, k_cells, k_cells_bwd, status):
             ctx.save_for_backward(x, knots, values)
-            ctx.k_cells_bwd = k_cells_bwd
-            return pwl_channels_forward(knots, values, x.contiguous(), k_cells=k_cells)
+            ctx.k_cells_bwd, ctx.status = k_cells_bwd, status
+            return pwl_channels_forward(knots, values, x.contiguous(), k_cells=k_cells, status=status)
 
         @staticmethod
         def backward(ctx, gy):
             x, knots, values = ctx.saved_tensors
             gv = torch.zeros_like(values) if ctx.needs_input_grad[2] else None
             gk = torch.zeros_like(knots) if ctx.needs_input_grad[1] else None
-            gx = pwl_channels_backward(knots, values, x.contiguous(), gy.contiguous().float(), None, gv, gk,
-                                       k_cells=ctx.k_cells_bwd)
-            return gx, gk, gv, None, None
+            # the backward kernel takes FP32 streams: a BF16 map's x and gy
+            # are widened (exactly) and gx is returned in x's dtype
+            gx = pwl_channels_backward(knots, values, x.contiguous().float(), gy.contiguous().float(), None, gv, gk,
+                                       k_cells=ctx.k_cells_bwd, status=ctx.status)
+            return gx.to(x.dtype), gk, gv, None, None, None
 
     _FUNCS["table"] = _TableFn
     _FUNCS["channels"] = _ChannelFn
@@ -539,9 +541,32 @@ class PWLFunction:
 
 class ChannelPWL:
     """Channel-wise learnable CPWL map with autograd: y[r, c] = v_c(x[r, c])
-    for x [R, C] (float32), knots and values [C, N+1] (float32 leaf tensors).
-    The backward gives gradients w.r.t. x, the values and the knots."""
+    for x [R, C] (float32 or bfloat16), knots and values [C, N+1] (float32
+    leaf tensors).  The backward gives gradients w.r.t. x (in x's dtype), the
+    values and the knots.
+
+    status: an int32 CUDA tensor of one element that the forward and backward
+    kernels OR their status bits into (bit 0: a channel's knots are not
+    strictly increasing, e.g. after a training step crossed two knots; the
+    results of that step are then unspecified).  The caller zeroes it and
+    reads it with ChannelPWL.check(status) between steps, where a host
+    synchronisation costs nothing; None gives each call a status word that
+    nothing reads."""
 
     @staticmethod
-    def apply(x, knots, values, k_cells: int = 0, k_cells_backward: int = 0):
-        return _autograd_classes()["channels"].apply(x, knots, values, k_cells, k_cells_backward)
+    def apply(x, knots, values, k_cells: int = 0, k_cells_backward: int = 0, status=None):
+        return _autograd_classes()["channels"].apply(x, knots, values, k_cells, k_cells_backward, status)
+
+    @staticmethod
+    def new_status(device="cuda"):
+        return _torch().zeros(1, dtype=_torch().int32, device=device)
+
+    @staticmethod
+    def check(status) -> None:
+        """Raises PwlError (PWL_EINVAL) if a kernel set a status bit since the
+        word was zeroed (synchronizes with the device)."""
+        bits = int(status.item())
+        if bits & 1:
+            raise PwlError(1, "ChannelPWL", "a channel's knots are not strictly increasing")
+        if bits:
+            raise PwlError(1, "ChannelPWL", f"status bits {bits:#x}")

@@ -399,7 +399,8 @@ __device__ __forceinline__ float clamp_nan(float x, float a, float b)
 // host round trip).
 struct TableHeader {
     int32_t status;      // bit 0: knots not strictly increasing; bit 1: non-finite knot or value;
-                         // bit 2: slope or reciprocal length not finite in FP32
+                         // bit 2: slope or reciprocal length not finite in FP32;
+                         // bit 3: an update moved an end knot
     uint32_t hmin_bits;  // shortest interval (positive float, ordered as uint)
     int32_t n_chain_b;   // backward index: chain records after the K_b cell records
     int32_t max_chain_b; // backward index: most chain hops any query can need

@@ -516,7 +516,18 @@ pwl_status launch_synth(pwl_table t, uint32_t seed, int64_t m, double* sum, cuda
     return PWL_OK;
 }
 
-pwl_status ensure_texture(pwl_table t)
+// The texels are the table's rounded values (FP32, or FP16 for FP16
+// tables), copied on the caller's stream after the kernels that wrote them.
+pwl_status copy_texels(pwl_table t, cudaStream_t s)
+{
+    const bool half_texels = (t->dtype == PWL_FP16);
+    const void* src = half_texels ? t->vstore : (const void*)t->vk;
+    const size_t row = (half_texels ? 2 : 4) * (size_t)(t->N + 1);
+    PWL_CUDA_TRY(cudaMemcpy2DToArrayAsync(t->tex_array, 0, 0, src, row, row, 1, cudaMemcpyDeviceToDevice, s));
+    return PWL_OK;
+}
+
+pwl_status ensure_texture(pwl_table t, cudaStream_t s)
 {
     if (t->tex) return PWL_OK;
     int maxa = 0;
@@ -526,10 +537,14 @@ pwl_status ensure_texture(pwl_table t)
     const bool half_texels = (t->dtype == PWL_FP16);
     cudaChannelFormatDesc cd = half_texels ? cudaCreateChannelDescHalf() : cudaCreateChannelDesc<float>();
     PWL_CUDA_TRY(cudaMallocArray(&t->tex_array, &cd, (size_t)t->N + 1, 0));
-    const void* src = half_texels ? t->vstore : (const void*)t->vk;
-    const size_t esz = half_texels ? 2 : 4;
-    PWL_CUDA_TRY(cudaMemcpy2DToArray(t->tex_array, 0, 0, src, esz * (t->N + 1), esz * (t->N + 1), 1,
-                                     cudaMemcpyDeviceToDevice));
+    // from here on a failure frees the array, so that a later call starts afresh
+    auto undo = [&](pwl_status st) {
+        cudaFreeArray(t->tex_array);
+        t->tex_array = nullptr;
+        return st;
+    };
+    pwl_status st = copy_texels(t, s);
+    if (st != PWL_OK) return undo(st);
     cudaResourceDesc rd{};
     rd.resType = cudaResourceTypeArray;
     rd.res.array.array = t->tex_array;
@@ -538,11 +553,20 @@ pwl_status ensure_texture(pwl_table t)
     td.filterMode = cudaFilterModeLinear;
     td.readMode = cudaReadModeElementType;
     td.normalizedCoords = 0;
-    PWL_CUDA_TRY(cudaCreateTextureObject(&t->tex, &rd, &td, nullptr));
+    cudaError_t e = cudaCreateTextureObject(&t->tex, &rd, &td, nullptr);
+    if (e != cudaSuccess) {
+        t->tex = 0;
+        return undo(cuda_fail(e, "cudaCreateTextureObject"));
+    }
     return PWL_OK;
 }
 
 }  // namespace
+
+pwl_status refresh_texture(pwl_table t, cudaStream_t s)
+{
+    return t->tex ? copy_texels(t, s) : PWL_OK;
+}
 
 }  // namespace pwl
 
@@ -603,7 +627,7 @@ pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* 
         PWL_CHECK_LAUNCH("eval_search_kernel");
         return PWL_OK;
     }
-    st = ensure_texture(t);
+    st = ensure_texture(t, s);
     if (st != PWL_OK) return st;
     const size_t fixed = sizeof(float) * (size_t)(t->N + 2);
     if (fixed + 1024 > di.smem_optin) return fail(PWL_ENOTSUP, "table too large for the texture path");

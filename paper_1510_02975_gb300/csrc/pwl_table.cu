@@ -56,7 +56,7 @@ __device__ __forceinline__ int block_exclusive_scan_int(int v, int* s_warp, int*
 
 __global__ void __launch_bounds__(kBuildThreads) table_round_kernel(
     const double* __restrict__ knots, const double* __restrict__ values, int N, int dtype, float* xk,
-    float* vk, void* vstore, float* slope, float* inv_h, TableHeader* hdr)
+    float* vk, void* vstore, float* slope, float* inv_h, TableHeader* hdr, int check_ends, float a, float b)
 {
     __shared__ int s_status;
     __shared__ unsigned s_hmin;
@@ -107,6 +107,9 @@ __global__ void __launch_bounds__(kBuildThreads) table_round_kernel(
         slope[N + 1] = __double2float_rn(((double)vk[N] - (double)vk[N - 1]) / hN);
         inv_h[N + 1] = __double2float_rn(1.0 / hN);
     }
+    // an update keeps the cell grids of the build, which span [a, b]: the
+    // rounded end knots must not move (bit 3 otherwise)
+    if (check_ends && threadIdx.x == 0 && !(xk[0] == a && xk[N] == b)) st |= 8;
     if (st) atomicOr(&s_status, st);
     if (hmin > 0.0f) atomicMin(&s_hmin, __float_as_uint(hmin));
     else atomicMin(&s_hmin, 0u);
@@ -173,7 +176,10 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_b_kernel(
             j = lb;
             chained = (j < N && cj[j + 1] == c);
         } else {
-            j = lb - 1;  // cell 0 holds knot 0 and cell K-1 knot N, so 0 <= j < N here
+            // cell 0 holds knot 0 and cell K-1 knot N, so 0 <= j < N here; the
+            // clamp keeps the reads in range after an update that moved x_0
+            // (status bit 3, reported by pwl_table_check)
+            j = max(lb - 1, 0);
         }
         const float w = chained ? make_link(K + cpos[j + 1]) : slope[j + 1];
         rec16[c] = make_float4(xk[j], vk[j], slope[j], w);
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_f_kernel(
             // the line of interval j+1 through (x_j, v_j) with its FP32 slope,
             // valued at the anchor x_c (FP32: one FP64 division per cell would
             // dominate the build on this GPU's few FP64 units)
-            const int j = lb - 1;
+            const int j = max(lb - 1, 0);  // >= 0 unless an update moved x_0 (status bit 3)
             const float xc = __fmaf_rn(__int2float_rn(c), w, a);
             const float s = slope[j + 1];
             recP[c] = make_float2(__fmaf_rn(__fsub_rn(xc, xk[j]), s, vk[j]), s);
@@ -245,7 +251,7 @@ pwl_status launch_build(pwl_table t, const double* d_knots, const double* d_valu
     const int N = (int)t->N;
     if (!index_only) {
         table_round_kernel<<<1, kBuildThreads, 0, s>>>(d_knots, d_values, N, t->dtype, t->xk, t->vk, t->vstore,
-                                                       t->slope, t->inv_h, t->hdr);
+                                                       t->slope, t->inv_h, t->hdr, 1, t->a, t->b);
         PWL_CHECK_LAUNCH("table_round_kernel");
     }
     table_index_b_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->Kb, t->inv_w_b, t->off_b, t->xk, t->vk, t->slope,
@@ -262,6 +268,9 @@ pwl_status status_error(const TableHeader& h)
     if (h.status & 1) return fail(PWL_EINVAL, "knots are not strictly increasing after rounding to FP32");
     if (h.status & 2) return fail(PWL_EINVAL, "a knot or value is not finite");
     if (h.status & 4) return fail(PWL_EINVAL, "a slope or reciprocal length overflows FP32");
+    if (h.status & 8)
+        return fail(PWL_EINVAL, "an update moved the end knots x_0 or x_N (after rounding to FP32); the table "
+                                "keeps the cell grid of its build over [x_0, x_N]: build a new table instead");
     return PWL_OK;
 }
 
@@ -397,7 +406,7 @@ pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_
     };
 
     table_round_kernel<<<1, kBuildThreads, 0, s>>>(d_knots, d_values, N, value_dtype, t->xk, t->vk,
-                                                   t->vstore, t->slope, t->inv_h, t->hdr);
+                                                   t->vstore, t->slope, t->inv_h, t->hdr, 0, 0.0f, 0.0f);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(e, "table_round_kernel"));
     TableHeader h{};
     float ab[2];
@@ -447,7 +456,9 @@ pwl_status pwl_table_update(pwl_table t, const double* d_knots, const double* d_
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
-    return launch_build(t, d_knots, d_values, false, as_stream(stream));
+    const pwl_status st = launch_build(t, d_knots, d_values, false, as_stream(stream));
+    if (st != PWL_OK) return st;
+    return refresh_texture(t, as_stream(stream));
 }
 
 pwl_status pwl_table_check(pwl_table t, void* stream)

@@ -32,6 +32,9 @@ inline size_t eval16_smem_bytes(const pwl_table_s* t) { return sizeof(float4) * 
 int64_t forward_cell_capacity(int64_t N, size_t budget);
 int64_t backward_cell_capacity(int64_t N);
 void choose_cells(pwl_table t, float hmin, int64_t requested);
+// Re-copies the rounded values into the texture of the comparison path, if
+// the table has one (after an in-place update), on stream s.
+pwl_status refresh_texture(pwl_table t, cudaStream_t s);
 
 // Backward: K_b + reserved chain records, N+2 reciprocal lengths and
 // 2 (N+2) FP32 accumulators per copy.  The accumulators have L copies (lane l

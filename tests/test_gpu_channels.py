@@ -154,3 +154,51 @@ def test_channel_autograd_matches_finite_differences(pwl):
             if 0 < j < N:
                 fd_k = (loss(k32 + dv, v32) - loss(k32 - dv, v32)) / (2 * eps)
                 assert abs(kt.grad[c, j].item() - fd_k) <= 1e-3 * max(1.0, abs(fd_k))
+
+
+def test_channel_autograd_bf16_input(pwl):
+    # a BF16 map differentiates too: gx comes back in BF16, and the gradients
+    # equal the FP32 backward's on the widened inputs (BF16 -> FP32 is exact)
+    C, N, R = 24, 64, 2001
+    knots, values = _channel_tables(pwl, C, N, seed=9)
+    g = torch.Generator(device="cuda").manual_seed(10)
+    x16 = (torch.randn(R, C, generator=g, device="cuda") * 2.0).to(torch.bfloat16).requires_grad_(True)
+    gy = torch.randn(R, C, generator=g, device="cuda").to(torch.bfloat16)
+    kt = torch.tensor(knots, device="cuda", requires_grad=True)
+    vt = torch.tensor(values, device="cuda", requires_grad=True)
+    st = pwl.ChannelPWL.new_status()
+    y = pwl.ChannelPWL.apply(x16, kt, vt, status=st)
+    assert y.dtype == torch.bfloat16
+    y.backward(gy)
+    pwl.ChannelPWL.check(st)
+    assert x16.grad.dtype == torch.bfloat16
+    gv = torch.zeros(C, N + 1, device="cuda")
+    gk = torch.zeros(C, N + 1, device="cuda")
+    gx = pwl.pwl_channels_backward(kt.detach(), vt.detach(), x16.detach().float(), gy.float(), None, gv, gk)
+    assert torch.equal(x16.grad, gx.to(torch.bfloat16))
+    xs = x16.detach().float().cpu().numpy().astype(np.float64)
+    gys = gy.float().cpu().numpy().astype(np.float64)
+    for c in range(C):
+        _, rgv, rgk, rva, rka = oracle.evaluate_grad(knots[c].astype(np.float64), values[c].astype(np.float64),
+                                                     xs[:, c], gys[:, c])
+        assert np.all(np.abs(vt.grad[c].cpu().numpy() - rgv) <= GRAD_REL * rva + 1e-30)
+        assert np.all(np.abs(kt.grad[c].cpu().numpy() - rgk) <= GRAD_REL * rka + 1e-30)
+
+
+def test_channel_autograd_reports_crossed_knots(pwl):
+    # a training step that makes two knots of a channel cross is visible to
+    # the caller through the status word of the autograd path
+    C, N, R = 16, 32, 256
+    knots, values = _channel_tables(pwl, C, N, seed=11)
+    knots[7, 10], knots[7, 11] = knots[7, 11], knots[7, 10]
+    kt = torch.tensor(knots, device="cuda", requires_grad=True)
+    vt = torch.tensor(values, device="cuda", requires_grad=True)
+    x = torch.zeros(R, C, device="cuda", requires_grad=True)
+    st = pwl.ChannelPWL.new_status()
+    pwl.ChannelPWL.apply(x, kt, vt, status=st).sum().backward()
+    with pytest.raises(pwl.PwlError, match="not strictly increasing"):
+        pwl.ChannelPWL.check(st)
+    st.zero_()
+    ok = pwl.ChannelPWL.new_status()
+    pwl.ChannelPWL.apply(x, torch.tensor(_channel_tables(pwl, C, N, seed=11)[0], device="cuda"), vt, status=ok)
+    pwl.ChannelPWL.check(ok)

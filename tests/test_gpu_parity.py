@@ -357,15 +357,51 @@ def test_table_update_in_place(pwl, workloads):
     N = 512
     k1 = pwl.pwl_design(f1, N)
     t = pwl.Table(k1, pwl.pwl_project(f1, k1, "project"))
+    x = workloads.uniform_queries(f2, 300001, seed=9)
+    t.variant(1, x)  # creates the texture of the comparison path from the first function
     k2 = pwl.pwl_design(f2, N)
     v2 = pwl.pwl_project(f2, k2, "project")
-    t.update(k2, v2)
+    # on a non-blocking stream: the texture refresh must follow the update there
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        t.update(k2, v2)
+        y_tex = t.variant(1, x)
+    torch.cuda.current_stream().wait_stream(s)
     pwl.pwl_table_check(t.handle)
-    x = workloads.uniform_queries(f2, 300001, seed=9)
     xk, vk = round_knots(k2.cpu().numpy()), round_values(v2.cpu().numpy(), "fp32")
     _check_eval(t(x), xk, vk, x)
     for mode in (2, 3):
         _check_eval(t.variant(mode, x), xk, vk, x)
+    # the texture filter follows the new values (8-bit weight bound)
+    xs = x.cpu().numpy().astype(np.float64)
+    ref = oracle.evaluate(xk, vk, xs)
+    i = np.clip(np.searchsorted(xk, xs, side="right"), 1, len(xk) - 1)
+    dv = np.abs(vk[i] - vk[i - 1])
+    y = y_tex.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(y - ref) <= dv / 256.0 + 1e-6 * np.abs(vk).max())
+    t.close()
+
+
+def test_table_update_moving_an_end_knot_is_reported(pwl, workloads):
+    # the cell grids of a table span the built [x_0, x_N]: an update that
+    # moves an end knot is flagged by pwl_table_check, and a valid update
+    # afterwards clears the flag
+    f = workloads.GAUSSIAN
+    N = 256
+    k = pwl.pwl_design(f, N)
+    v = pwl.pwl_project(f, k, "project")
+    t = pwl.Table(k, v)
+    for end in (0, N):
+        k2 = k.clone()
+        k2[end] += 0.25 * float(k[1] - k[0]) * (1 if end == 0 else -1)
+        t.update(k2, v)
+        with pytest.raises(pwl.PwlError, match="end knots"):
+            pwl.pwl_table_check(t.handle)
+    t.update(k, v)
+    pwl.pwl_table_check(t.handle)
+    x = workloads.uniform_queries(f, 100003, seed=2)
+    _check_eval(t(x), round_knots(k.cpu().numpy()), round_values(v.cpu().numpy(), "fp32"), x)
     t.close()
 
 
