@@ -264,15 +264,25 @@ pwl_status pwl_eval(pwl_table t, const void* d_x, void* d_y, int64_t m, int32_t 
                     void* stream);
 
 /* Comparison paths for the measurements of Section V-A (Table I):
- *   mode 0: Algorithm 1 with the binary search of Section IV on the FP32
- *           knot table in shared memory (O(log N) per query);
- *   mode 1: the same interval search as pwl_eval, then the texture unit's
+ *   mode 0: Algorithm 1 with the search of Section IV: a binary search over
+ *           the FP32 knots in shared memory, unrolled at compile time for
+ *           2^L >= N+1 knot slots (L <= 14, so N <= 16383) with selects in
+ *           place of branches; delta by a division; (1 - delta) v_{i-1} +
+ *           delta v_i (O(log N) per query);
+ *   mode 1: the same interval lookup as pwl_eval, then the texture unit's
  *           linear filter at coordinate i - 1 + delta + 1/2 over the values
  *           (Section IV-B); the filter weight is fixed point (8 fractional
  *           bits), so results differ from pwl_eval by up to |v_i - v_{i-1}|/256;
  *   mode 2, 3: pwl_eval forced to its 8-byte or 16-byte cell index (it
- *           otherwise picks one per table, see pwl_table_info.layout).
- * x, y: device FP32 arrays of m elements.                                  */
+ *           otherwise picks one per table, see pwl_table_info.layout);
+ *   mode 4: the search of mode 0, then the texture filter of mode 1 (Table
+ *           I's optimized partition with hardware interpolation);
+ *   mode 5: the uniform-partition lookup of Section IV with the texture
+ *           filter: coordinate (x - x_0) N / (x_N - x_0) + 1/2, no search;
+ *           correct only for a table whose knots are uniform (e.g. built
+ *           from x_i = a + i (b - a)/N), up to the 8-bit weight.
+ * x, y: device FP32 arrays of m elements.  The texture of modes 1, 4, 5 is
+ * created on first use (an allocation) and refreshed by pwl_table_update.  */
 pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* d_y, int64_t m,
                             void* stream);
 
@@ -287,6 +297,42 @@ pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* 
  * adds the FP32 sum of its results (in an unspecified order) to *d_sum, a
  * device FP64 word the caller zeroes: a checksum that keeps the work live.  */
 pwl_status pwl_eval_synthetic(pwl_table t, uint32_t seed, int64_t m, double* d_sum, void* stream);
+
+/* pwl_eval_synthetic for the comparison paths of pwl_eval_variant (modes
+ * 0..5, same queries and checksum): the compute ceilings of Table I's rows
+ * on this GPU (binary search vs cell index, lerp vs texture filter).       */
+pwl_status pwl_eval_synthetic_variant(pwl_table t, int32_t mode, uint32_t seed, int64_t m, double* d_sum,
+                                      void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Direct evaluation of f: the comparison systems of Section V               */
+/* ------------------------------------------------------------------------ */
+
+/* y[q] = f(x[q]) computed directly in FP32, the alternatives the paper
+ * times against the CPWL evaluation (Table I; Sections V-B and V-C):
+ *   PWL_F_GAUSSIAN    method 0: A expf(-u^2/2), u = (x - mu)(1/s)
+ *                     method 1: the same with the SFU's __expf
+ *   PWL_F_LORENTZIAN  method 0: A / (1 + u^2), u = (x - x0)(1/g), IEEE division
+ *                     method 1: the same with __fdividef (fast division)
+ *   PWL_F_BESSEL_J0   method 0: A j0f(alpha x) (the CUDA math library)
+ *                     method 1: the first term of the asymptotic expansion,
+ *                     A sqrt(2/pi) rsqrtf(z) __cosf(z - pi/4), z = alpha x
+ *                     (valid for z >> 1/4; its error decays like z^{-3/2};
+ *                     z <= 0 gives inf or NaN)
+ * with the parameters of pwl_kind (A, mu, 1/s, x0, 1/g, alpha and
+ * A sqrt(2/pi) formed in FP64 and rounded to FP32 once).  No clamping to
+ * [a, b]: f is evaluated at x as given.  x, y: device FP32 arrays of m
+ * elements (any alignment; y may be x), streamed like pwl_eval.  Errors:
+ * PWL_EINVAL (descriptor, method, sizes, NULL), PWL_ENOTSUP (other kinds).   */
+pwl_status pwl_direct_eval(const pwl_func* f, int32_t method, const float* d_x, float* d_y, int64_t m,
+                           void* stream);
+
+/* The compute ceiling of pwl_direct_eval: f at the m register-generated
+ * queries of pwl_eval_synthetic (x_q = u_q (b - a) + a with a, b the FP32
+ * roundings of f->a, f->b), every CTA adding the FP32 sum of its results to
+ * *d_sum (device FP64 word, zeroed by the caller).                          */
+pwl_status pwl_direct_synthetic(const pwl_func* f, int32_t method, uint32_t seed, int64_t m, double* d_sum,
+                                void* stream);
 
 /* Backward of pwl_eval for upstream gradients gy (FP32, m elements):
  *   gx[q] = gy[q] * s_i (s_i the slope of x[q]'s interval; 0 if clamped)
@@ -447,6 +493,32 @@ pwl_status pwl_channels_backward(const float* d_knots, const float* d_values, in
                                  int64_t n_intervals, int64_t k_cells, const float* d_x, const float* d_gy,
                                  float* d_gx, float* d_g_values, float* d_g_knots, int64_t rows,
                                  int32_t* d_status, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Failure injection: tests of the error paths (no counterpart in the paper;  */
+/* nothing here faults or hangs a GPU)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Makes the library's device allocations fail: succeed_first = n >= 0 lets
+ * the next n allocations (cudaMalloc / cudaMallocArray inside pwl_table_build,
+ * pwl_batch_create, pwl_batch_plan and the texture of pwl_eval_variant)
+ * through and fails every later one with PWL_ENOMEM, until the hook is reset
+ * with succeed_first < 0.  A failing call releases what it had allocated and
+ * leaves its output handle NULL (or the existing plan / texture unchanged).
+ * Process-wide; host only; always PWL_OK.                                   */
+pwl_status pwl_test_fail_allocations(int64_t succeed_first);
+
+/* Makes the bounded waits of the asynchronous batch evaluation (shape 4 of
+ * pwl_batch_plan) run out, to test their timeout path.  withhold = 1: every
+ * staging barrier of the following pwl_batch_eval launches expects one
+ * arrival more than the kernel makes, so the first wait for a staging copy
+ * of each CTA gives up after wait_limit_ns; the CTA then makes the withheld
+ * arrival, waits (bounded) for its bulk copies to land, stops, and
+ * pwl_batch_check reports PWL_ETIMEOUT (its results are incomplete).
+ * withhold = 0 restores normal operation; wait_limit_ns 0 restores the
+ * default limit of 1 s (at most 1 s).  Host only; takes effect at the next
+ * pwl_batch_eval.  Errors: PWL_EINVAL (NULL batch, arguments).             */
+pwl_status pwl_batch_inject_wait_timeout(pwl_batch b, int32_t withhold, uint64_t wait_limit_ns);
 
 /* pwl_eval_backward for callers that cannot allocate device memory (the
  * paper has no counterpart; this is a library concern): real-time loops that

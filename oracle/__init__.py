@@ -61,6 +61,8 @@ def _load():
         sig = {
             "orc_f": (ctypes.c_double, [F, ctypes.c_double]),
             "orc_f2": (ctypes.c_double, [F, ctypes.c_double]),
+            "orc_f_many": (None, [F, D, i64, D]),
+            "orc_j0_one_term": (None, [F, D, i64, D]),
             "orc_density": (None, [F, i64, D]),
             "orc_cumulative": (None, [D, i64, ctypes.c_double, D]),
             "orc_invert": (ctypes.c_int, [D, D, i64, ctypes.c_double, ctypes.c_double, i64, D]),
@@ -117,6 +119,26 @@ def f(desc, x):
     lib, F = _load(), _func(desc)
     xs = np.atleast_1d(_f64(x))
     return np.array([lib.orc_f(ctypes.byref(F), float(v)) for v in xs])
+
+
+def f_many(desc, x) -> np.ndarray:
+    """f at every point of x (one C call; same values as f())."""
+    lib, F = _load(), _func(desc)
+    xs = _f64(np.atleast_1d(x)).ravel()
+    out = np.empty_like(xs)
+    lib.orc_f_many(ctypes.byref(F), _dp(xs), xs.size, _dp(out))
+    return out
+
+
+def j0_one_term(desc, x) -> np.ndarray:
+    """A sqrt(2/(pi z)) cos(z - pi/4), z = alpha x: the one-term asymptotic
+    form of A J0(alpha x) that the paper times (Section V-C); desc is a
+    bessel_j0 descriptor."""
+    lib, F = _load(), _func(desc)
+    xs = _f64(np.atleast_1d(x)).ravel()
+    out = np.empty_like(xs)
+    lib.orc_j0_one_term(ctypes.byref(F), _dp(xs), xs.size, _dp(out))
+    return out
 
 
 def f2(desc, x):

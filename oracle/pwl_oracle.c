@@ -20,6 +20,7 @@
  *   - CPWL evaluation                                      (Algorithm 1)
  *   - gradients of Algorithm 1 w.r.t. x, v(x_i), x_i        (calculus on Eq. 8)
  *   - L2 distances for the error results                   (Results 1-6)
+ *   - the direct evaluations the paper compares against    (Section V)
  *
  * Readings of points the paper leaves open (each listed in the design notes):
  *   - the density uses |f''| (Eq. 16 has the absolute value, Eq. 18 drops it);
@@ -144,6 +145,25 @@ double orc_f(const orc_func* F, double x)
  *                 J1(z)/z -> 1/2 as z -> 0)
  *   poly       : sum k (k-1) p_k x^(k-2)
  *   exp        : A lambda^2 exp(lambda x)                                 */
+/* f at n points (the reference of the direct-evaluation comparisons). */
+void orc_f_many(const orc_func* F, const double* x, int64_t n, double* out)
+{
+    for (int64_t q = 0; q < n; ++q) out[q] = orc_f(F, x[q]);
+}
+
+/* The first term of the asymptotic expansion of J0 for large argument that
+ * the paper times as a fast alternative to J0 (Section V-C):
+ *     A J0(z) ~ A sqrt(2 / (pi z)) cos(z - pi/4),  z = alpha x,
+ * evaluated as written (z > 0; the expression is the definition, its error
+ * against J0 is that of the truncated expansion). */
+void orc_j0_one_term(const orc_func* F, const double* x, int64_t n, double* out)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        const double z = F->p[1] * x[q];
+        out[q] = F->p[0] * sqrt(2.0 / (M_PI * z)) * cos(z - M_PI / 4.0);
+    }
+}
+
 double orc_f2(const orc_func* F, double x)
 {
     switch (F->kind) {

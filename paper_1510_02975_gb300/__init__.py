@@ -18,11 +18,13 @@ from ._capi import (DTYPES, FORMS, KINDS, PRECISIONS, PwlBatchInfo, PwlError, Pw
 
 __all__ = [
     "PwlError", "pwl_design", "pwl_project", "pwl_table_build", "pwl_table_update", "pwl_table_check", "pwl_table_destroy", "pwl_table_get_info",
-    "pwl_eval", "pwl_eval_variant", "pwl_eval_synthetic", "pwl_eval_backward", "pwl_eval_backward_noalloc",
+    "pwl_eval", "pwl_eval_variant", "pwl_eval_synthetic", "pwl_eval_synthetic_variant", "pwl_direct_eval",
+    "pwl_direct_synthetic", "pwl_eval_backward", "pwl_eval_backward_noalloc",
     "pwl_error_constants", "pwl_predicted_error", "pwl_n_for_error",
     "pwl_batch_create", "pwl_batch_destroy", "pwl_batch_design", "pwl_batch_project", "pwl_batch_build",
     "pwl_batch_check", "pwl_batch_plan", "pwl_batch_eval", "pwl_batch_autotune", "pwl_batch_get_info", "Batch",
-    "pwl_channels_forward", "pwl_channels_backward", "ChannelPWL", "Table", "design", "project", "PWLFunction",
+    "pwl_channels_forward", "pwl_channels_backward", "ChannelPWL", "pwl_test_fail_allocations",
+    "pwl_batch_inject_wait_timeout", "Table", "design", "project", "PWLFunction",
     "KINDS", "FORMS", "DTYPES", "PRECISIONS",
 ]
 
@@ -176,6 +178,48 @@ def pwl_eval_synthetic(handle, m: int, seed: int = 0, out=None, stream=None):
     return out
 
 
+def pwl_eval_synthetic_variant(handle, mode: int, m: int, seed: int = 0, out=None, stream=None):
+    """pwl_eval_synthetic for the comparison paths of pwl_eval_variant (modes 0..5)."""
+    torch = _torch()
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _require(out, torch.float64, "out", 1)
+    check(load().pwl_eval_synthetic_variant(ctypes.c_void_p(handle), int(mode), int(seed) & 0xFFFFFFFF, int(m),
+                                            _ptr(out), _stream(stream)), "pwl_eval_synthetic_variant")
+    return out
+
+
+DIRECT_METHODS = {"library": 0, "fast": 1}
+
+
+def pwl_direct_eval(f, method: str, x, y=None, stream=None):
+    """y = f(x) evaluated directly in FP32 (the paper's comparison systems):
+    method "library" (expf, IEEE division, j0f) or "fast" (__expf,
+    __fdividef, the one-term asymptotic J0 with __cosf and rsqrtf)."""
+    torch = _torch()
+    _require(x, torch.float32, "x")
+    if y is None:
+        y = torch.empty_like(x)
+    _require(y, torch.float32, "y", x.numel())
+    F = make_func(f)
+    check(load().pwl_direct_eval(ctypes.byref(F), DIRECT_METHODS[method], _ptr(x), _ptr(y), x.numel(),
+                                 _stream(stream)), "pwl_direct_eval")
+    return y
+
+
+def pwl_direct_synthetic(f, method: str, m: int, seed: int = 0, out=None, stream=None):
+    """Compute ceiling of pwl_direct_eval: f at m register-generated queries;
+    returns (or adds into `out`) the float64 checksum."""
+    torch = _torch()
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _require(out, torch.float64, "out", 1)
+    F = make_func(f)
+    check(load().pwl_direct_synthetic(ctypes.byref(F), DIRECT_METHODS[method], int(seed) & 0xFFFFFFFF, int(m),
+                                      _ptr(out), _stream(stream)), "pwl_direct_synthetic")
+    return out
+
+
 def pwl_error_constants(f, m_cells: int = 0, out=None, stream=None):
     """The integrals of |f''|^{2/5} and f''^2 over [a, b] (Results 4-6),
     midpoint rule on m_cells cells -> float64 (2,) on the GPU."""
@@ -315,6 +359,19 @@ def pwl_batch_autotune(handle, x, y, reps: int = 3, stream=None) -> dict:
           "pwl_batch_autotune")
     return {(shape, stage_min): float(t[4 * shape + j])
             for shape in range(5) for j, stage_min in enumerate((0, 4, 16, 64))}
+
+
+def pwl_test_fail_allocations(succeed_first: int) -> None:
+    """Failure injection: the next succeed_first device allocations of the
+    library succeed and later ones fail with PWL_ENOMEM (< 0 resets)."""
+    check(load().pwl_test_fail_allocations(int(succeed_first)), "pwl_test_fail_allocations")
+
+
+def pwl_batch_inject_wait_timeout(handle, withhold: bool, wait_limit_ns: int = 0) -> None:
+    """Failure injection: the asynchronous batch shape's staging waits run out
+    after wait_limit_ns (withhold=True); withhold=False restores them."""
+    check(load().pwl_batch_inject_wait_timeout(ctypes.c_void_p(handle), int(bool(withhold)), int(wait_limit_ns)),
+          "pwl_batch_inject_wait_timeout")
 
 
 def pwl_batch_get_info(handle) -> dict:

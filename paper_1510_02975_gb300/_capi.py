@@ -72,6 +72,9 @@ SIGNATURES = {
     "pwl_eval": (_ST, [_P, _P, _P, _I64, _I32, _P]),
     "pwl_eval_variant": (_ST, [_P, _I32, _P, _P, _I64, _P]),
     "pwl_eval_synthetic": (_ST, [_P, ctypes.c_uint32, _I64, _P, _P]),
+    "pwl_eval_synthetic_variant": (_ST, [_P, _I32, ctypes.c_uint32, _I64, _P, _P]),
+    "pwl_direct_eval": (_ST, [ctypes.POINTER(PwlFunc), _I32, _P, _P, _I64, _P]),
+    "pwl_direct_synthetic": (_ST, [ctypes.POINTER(PwlFunc), _I32, ctypes.c_uint32, _I64, _P, _P]),
     "pwl_error_constants": (_ST, [ctypes.POINTER(PwlFunc), _I64, _P, _P]),
     "pwl_predicted_error": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_double)]),
     "pwl_n_for_error": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I32, _I32, ctypes.POINTER(_I64)]),
@@ -91,6 +94,8 @@ SIGNATURES = {
     "pwl_batch_get_info": (_ST, [_P, ctypes.POINTER(PwlBatchInfo)]),
     "pwl_channels_forward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _I64, _I32, _P, _P]),
     "pwl_channels_backward": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _I64, _P, _P]),
+    "pwl_test_fail_allocations": (_ST, [_I64]),
+    "pwl_batch_inject_wait_timeout": (_ST, [_P, _I32, ctypes.c_uint64]),
 }
 
 _lib = None

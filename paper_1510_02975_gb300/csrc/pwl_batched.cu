@@ -274,6 +274,8 @@ struct EvalParams {
     const float2* recS;
     int buf_stride;          // float2 records per shared-memory buffer (asynchronous staging)
     int* status;             // device word: bit 2 set if a wait for a staging copy timed out
+    uint64_t wait_ns;        // limit of one wait for a staging copy (asynchronous staging)
+    int withheld;            // failure injection: arrivals a staging barrier expects but never gets (0 or 1)
 };
 
 __device__ __forceinline__ Lookup lookup_of(const BatchFunc& g)
@@ -376,14 +378,19 @@ __global__ void __launch_bounds__(THREADS, MINB) batch_eval_kernel(const EvalPar
 // so the SM keeps streaming through the copy.  Every wait is bounded: on a
 // timeout the CTA records it in *status, waits (bounded) for its copies in
 // flight and stops.
+// Failure injection (p.withheld = 1): each staging barrier expects one
+// arrival more than the kernel makes, so no wait can succeed and the first
+// one runs out after p.wait_ns; after the timeout thread 0 makes the
+// withheld arrival, and the final waits then complete exactly when the
+// bulk copies have landed, so that no copy is in flight when the CTA exits.
 template <int U>
 __global__ void __launch_bounds__(1024, 1) batch_eval_async_kernel(const EvalParams p, const float* x, float* y)
 {
     extern __shared__ __align__(16) float2 s_idx[];
     __shared__ __align__(8) uint64_t s_bar[2];
     if (threadIdx.x == 0) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
+        mbar_init(&s_bar[0], 1 + p.withheld);
+        mbar_init(&s_bar[1], 1 + p.withheld);
         fence_mbar_init();
     }
     __syncthreads();
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(1024, 1) batch_eval_async_kernel(const EvalPar
         busy[bi] = true;
     };
     auto wait = [&](int bi) {
-        const bool ok = mbar_wait_bounded(&s_bar[bi], parity[bi]);
+        const bool ok = mbar_wait_bounded(&s_bar[bi], parity[bi], p.wait_ns);
         if (ok) {  // a copy that did not complete stays busy for the final wait
             parity[bi] ^= 1u;
             busy[bi] = false;
@@ -449,6 +456,13 @@ __global__ void __launch_bounds__(1024, 1) batch_eval_async_kernel(const EvalPar
             run_direct<U>(p, g, w, x, y);
     }
     // copies still in flight (only after a failed wait): wait for them, bounded
+    // (busy[] and failed are the same in every thread)
+    if (failed && p.withheld) {
+        if (threadIdx.x == 0)
+            for (int b = 0; b < 2; ++b)
+                if (busy[b]) mbar_arrive(&s_bar[b]);
+        __syncthreads();
+    }
     for (int b = 0; b < 2; ++b)
         if (busy[b]) wait(b);
     if (failed && threadIdx.x == 0) atomicOr(p.status, 4);
@@ -530,6 +544,8 @@ struct pwl_batch_s {
     int64_t n_items, n_staged;
     int64_t total_queries;
     bool planned;
+    uint64_t wait_ns;           // limit of one wait for a staging copy (kWaitLimitNs unless a test sets it)
+    int withheld;               // failure injection of pwl_batch_inject_wait_timeout
 };
 
 namespace {
@@ -648,6 +664,8 @@ pwl_status pwl_batch_create(const pwl_func* funcs, const int64_t* n_intervals, i
     }
     pwl_batch b = new (std::nothrow) pwl_batch_s();
     if (!b) return fail(PWL_ENOMEM, "host allocation failed");
+    b->wait_ns = kWaitLimitNs;
+    b->withheld = 0;
     cudaGetDevice(&b->device);
     const DeviceInfo& di = device_info();
     b->F = n_funcs;
@@ -718,7 +736,7 @@ pwl_status pwl_batch_create(const pwl_func* funcs, const int64_t* n_intervals, i
     static_assert(sizeof(sizes) / sizeof(sizes[0]) == sizeof(slots) / sizeof(slots[0]), "one size per slot");
     size_t total = 0;
     for (size_t s : sizes) total += s;
-    cudaError_t e = cudaMalloc(&b->dev, total);
+    cudaError_t e = dev_malloc(&b->dev, total);
     if (e != cudaSuccess) {
         batch_free(b);
         return cuda_fail(e, "cudaMalloc(batch)");
@@ -876,7 +894,7 @@ pwl_status pwl_batch_plan(pwl_batch b, const int64_t* query_offsets, int32_t sha
     void* dev = nullptr;
     const size_t bytes_items = align256(sizeof(WorkItem) * std::max<size_t>(items.size(), 1));
     const size_t bytes_range = align256(sizeof(int) * (size_t)(n_ranges + 1));
-    PWL_CUDA_TRY(cudaMalloc(&dev, bytes_items + bytes_range + sizeof(int)));
+    PWL_CUDA_TRY(dev_malloc(&dev, bytes_items + bytes_range + sizeof(int)));
     cudaError_t e = cudaSuccess;
     if (!items.empty()) e = cudaMemcpy(dev, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -918,7 +936,7 @@ pwl_status pwl_batch_eval(pwl_batch b, const float* d_x, float* d_y, void* strea
     const EvalShape& sh = kShapes[b->shape];
     PWL_CUDA_TRY(raise_smem_limit(sh.kern, b->smem));
     const EvalParams p{b->items, b->range, b->n_ranges, b->counter, b->bf, b->xk, b->recP, b->recS,
-                       b->buf_stride, b->status};
+                       b->buf_stride, b->status, b->wait_ns, b->withheld};
     if (sh.stage != kStageAsync)
         PWL_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), as_stream(stream)));
     sh.kern<<<b->grid, sh.threads, b->smem, as_stream(stream)>>>(p, d_x, d_y);
@@ -980,6 +998,17 @@ pwl_status pwl_batch_autotune(pwl_batch b, const float* d_x, float* d_y, int32_t
     cudaEventDestroy(e1);
     if (st != PWL_OK) return st;
     return pwl_batch_plan(b, qo.data(), best_shape, best_stage);
+}
+
+pwl_status pwl_batch_inject_wait_timeout(pwl_batch b, int32_t withhold, uint64_t wait_limit_ns)
+{
+    clear_error();
+    if (!b) return fail(PWL_EINVAL, "batch is NULL");
+    if (withhold != 0 && withhold != 1) return fail(PWL_EINVAL, "withhold must be 0 or 1");
+    if (wait_limit_ns > kWaitLimitNs) return fail(PWL_EINVAL, "wait limit above %llu ns", (unsigned long long)kWaitLimitNs);
+    b->withheld = withhold;
+    b->wait_ns = wait_limit_ns ? wait_limit_ns : kWaitLimitNs;
+    return PWL_OK;
 }
 
 pwl_status pwl_batch_get_info(pwl_batch b, pwl_batch_info* info)

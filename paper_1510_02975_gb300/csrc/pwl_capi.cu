@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -33,6 +34,32 @@ pwl_status cuda_fail(cudaError_t e, const char* what)
 {
     snprintf(g_err, sizeof(g_err), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
     return (e == cudaErrorMemoryAllocation) ? PWL_ENOMEM : PWL_ECUDA;
+}
+
+// Failure injection for the allocation paths: < 0 disables; n >= 0 lets
+// the next n device allocations through and fails every one after them.
+static std::atomic<int64_t> g_alloc_budget{-1};
+
+static bool alloc_allowed()
+{
+    int64_t b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) return false;
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return true;
+    }
+    return true;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes)
+{
+    if (!alloc_allowed()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_array(cudaArray_t* a, const cudaChannelFormatDesc* d, size_t width)
+{
+    if (!alloc_allowed()) return cudaErrorMemoryAllocation;
+    return cudaMallocArray(a, d, width, 0);
 }
 
 const DeviceInfo& device_info()
@@ -163,6 +190,13 @@ pwl_status pwl_func_sampled(double a, double b, const double* d_samples, int64_t
 }
 
 const char* pwl_last_error(void) { return pwl::g_err; }
+
+pwl_status pwl_test_fail_allocations(int64_t succeed_first)
+{
+    clear_error();
+    g_alloc_budget.store(succeed_first < 0 ? -1 : succeed_first);
+    return PWL_OK;
+}
 
 int32_t pwl_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 

@@ -55,6 +55,12 @@ inline cudaError_t raise_smem_limit(Kern kern, size_t smem)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Every device allocation of the library goes through these, so that a test
+// can make them fail (pwl_test_fail_allocations) and see each call that
+// allocates return PWL_ENOMEM and release what it had taken.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_malloc_array(cudaArray_t* a, const cudaChannelFormatDesc* d, size_t width);
+
 // ---------------------------------------------------------------------------
 // analytic functions: f and f'' (FP64 and FP32 versions)
 // ---------------------------------------------------------------------------

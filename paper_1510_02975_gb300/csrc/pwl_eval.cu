@@ -15,16 +15,26 @@
 // 16-byte index instead (one record {x_j, v_j, s_j, s_{j+1}} per cell, one
 // 16-byte load per query): fewer instructions, more shared-memory wavefronts.
 //
-// Comparison paths (pwl_eval_variant):
-//   mode 0  the paper's Algorithm 1: binary search over the FP32 knots in
-//           shared memory (Section IV), delta, (1 - delta) v_{i-1} + delta v_i
+// Comparison paths (pwl_eval_variant, and pwl_eval_synthetic_variant with
+// queries generated in registers):
+//   mode 0  the paper's Algorithm 1 with its search (Section IV): a binary
+//           search over the FP32 knots in shared memory, unrolled for the
+//           table's size and made of selects (no divergent branches), delta
+//           by a division, (1 - delta) v_{i-1} + delta v_i
 //   mode 1  interval lookup through the 16-byte index, then the texture
 //           unit's linear filter at i - 1 + delta + 1/2 (Section IV-B)
-//   mode 2, 3  the main path forced to the 8-byte or the 16-byte index.
+//   mode 2, 3  the main path forced to the 8-byte or the 16-byte index
+//   mode 4  the search of mode 0, then the texture filter (the paper's
+//           "optimized partition, hardware interpolation", Table I)
+//   mode 5  uniform partition: no search, the texture coordinate
+//           (x - x_0) N / (x_N - x_0) + 1/2 (Section IV's O(1) case with
+//           hardware interpolation, Table I); exact only for a table whose
+//           knots are uniform
 #include <math.h>
 
 #include <algorithm>
 
+#include "pwl_stream.cuh"
 #include "pwl_table.cuh"
 
 namespace pwl {
@@ -129,94 +139,10 @@ struct Lerp16 {
     }
 };
 
-// 16-byte vectors of each I/O type
-template <typename IO>
-struct Vec;
-template <>
-struct Vec<float> {
-    static constexpr int n = 4;
-    using T = float4;
-    template <class L>
-    static __device__ __forceinline__ T apply(T v, const L& f)
-    {
-        v.x = f(v.x);
-        v.y = f(v.y);
-        v.z = f(v.z);
-        v.w = f(v.w);
-        return v;
-    }
-    static __device__ __forceinline__ float to_f(float x) { return x; }
-    static __device__ __forceinline__ float from_f(float x) { return x; }
-};
-template <>
-struct Vec<__nv_bfloat16> {
-    static constexpr int n = 8;
-    using T = uint4;
-    template <class L>
-    static __device__ __forceinline__ T apply(T v, const L& f)
-    {
-        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float2 g = __bfloat1622float2(h[k]);
-            g.x = f(g.x);
-            g.y = f(g.y);
-            h[k] = __float22bfloat162_rn(g);
-        }
-        return v;
-    }
-    static __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
-    static __device__ __forceinline__ __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
-};
-template <>
-struct Vec<__half> {
-    static constexpr int n = 8;
-    using T = uint4;
-    template <class L>
-    static __device__ __forceinline__ T apply(T v, const L& f)
-    {
-        __half2* h = reinterpret_cast<__half2*>(&v);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float2 g = __half22float2(h[k]);
-            g.x = f(g.x);
-            g.y = f(g.y);
-            h[k] = __float22half2_rn(g);
-        }
-        return v;
-    }
-    static __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
-    static __device__ __forceinline__ __half from_f(float x) { return __float2half_rn(x); }
-};
-
-// streaming (evict-first) 16-byte global accesses
-__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
-__device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
-__device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
-__device__ __forceinline__ void st_stream(uint4* p, uint4 v) { __stcs(p, v); }
-
 template <typename IO, int U, class L>
 __device__ __forceinline__ void eval_body(const EvalArgs& p, const L& f, const IO* x, IO* y, int64_t m)
 {
-    using V = Vec<IO>;
-    using T = typename V::T;
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const T* xv = reinterpret_cast<const T*>(x + p.head);
-    T* yv = reinterpret_cast<T*>(y + p.head);
-    int64_t i = tid;
-    for (; i + (U - 1) * nthr < p.nvec; i += U * nthr) {
-        T v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = ld_stream(xv + i + u * nthr);
-#pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = V::apply(v[u], f);
-#pragma unroll
-        for (int u = 0; u < U; ++u) st_stream(yv + i + u * nthr, v[u]);
-    }
-    for (; i < p.nvec; i += nthr) st_stream(yv + i, V::apply(ld_stream(xv + i), f));
-    for (int64_t j = tid; j < p.head; j += nthr) y[j] = V::from_f(f(V::to_f(x[j])));
-    for (int64_t j = p.head + p.nvec * V::n + tid; j < m; j += nthr) y[j] = V::from_f(f(V::to_f(x[j])));
+    stream_body<IO, U>(p.head, p.nvec, f, x, y, m);
 }
 
 // LAYOUT 0: 8-byte index; 1: 16-byte index.  MINB = 2 asks for <= 32
@@ -257,33 +183,7 @@ __global__ void __launch_bounds__(1024, MINB) eval_kernel(const EvalArgs args, c
     }
 }
 
-// ---- compute ceiling: queries generated in registers -----------------------
-// The query stream of pwl_eval_synthetic: u_q = top 24 bits of lowbias32(q +
-// seed) / 2^24 (the 32-bit integer hash "lowbias32" of the hash-prospector
-// project: xor-shift 16, multiply 0x7feb352d, xor-shift 15, multiply
-// 0x846ca68b, xor-shift 16), x_q = u_q (b - a) + a in FP32 (two roundings).
-__device__ __forceinline__ uint32_t lowbias32(uint32_t x)
-{
-    x ^= x >> 16;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
-
-template <class L>
-__device__ __forceinline__ float synth_sum(const L& f, uint32_t seed, float a, float w, int64_t m)
-{
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    float acc = 0.0f;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += nthr) {
-        const float u = (float)(lowbias32((uint32_t)q + seed) >> 8) * 0x1p-24f;
-        acc += f(__fadd_rn(__fmul_rn(u, w), a));
-    }
-    return acc;
-}
-
+// ---- compute ceiling: queries generated in registers (pwl_stream.cuh) ------
 // Algorithm 1 on m generated queries: no query loaded, no result stored;
 // every CTA adds the sum of its results to *sum (FP64).  The staging and the
 // lookup are those of eval_kernel.
@@ -315,46 +215,105 @@ __global__ void __launch_bounds__(1024, MINB) eval_synth_kernel(const EvalArgs a
         acc = n_chain == 0 ? synth_sum(Lerp16<false>{s_fwd, p}, seed, p.a, w, m)
                            : synth_sum(Lerp16<true>{s_fwd, p}, seed, p.a, w, m);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     // the index may fill all of the shared memory: once every lookup is
     // done, its first 32 words hold the warp sums
-    float* s_red = reinterpret_cast<float*>(s_fwd);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += (double)s_red[k];
-        atomicAdd(sum, t);
-    }
+    cta_sum_to(acc, reinterpret_cast<float*>(s_fwd), sum);
 }
 
-// ---- mode 0: Algorithm 1 with a binary search over the knots --------------
-__global__ void __launch_bounds__(1024) eval_search_kernel(const float* __restrict__ xk_g,
-                                                           const float* __restrict__ vk_g, int N,
-                                                           const float* x, float* y, int64_t m)
+// ---- comparison paths (modes 0, 1, 4, 5) -----------------------------------
+// Every variant kernel runs either on a query stream (SYNTH = false: x -> y
+// with the streaming shape of pwl_eval) or on register-generated queries
+// (SYNTH = true: the sum of the results goes to *sum).
+struct StreamIO {
+    const float* x;
+    float* y;
+    int64_t m;
+    int64_t head, nvec;  // stream split (SYNTH = false)
+    uint32_t seed;       // query generator (SYNTH = true)
+    double* sum;
+};
+
+constexpr int kVarUnroll = 4;
+
+// s_red: 32 floats of shared memory free once every lookup is done
+template <bool SYNTH, class F>
+__device__ __forceinline__ void run_variant(const StreamIO& io, const F& f, float a, float b, float* s_red)
 {
-    extern __shared__ float2 s_kv[];  // (x_j, v_j)
-    for (int j = threadIdx.x; j <= N; j += blockDim.x) s_kv[j] = make_float2(xk_g[j], vk_g[j]);
-    __syncthreads();
-    const float a = s_kv[0].x, b = s_kv[N].x;
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += nthr) {
-        const float xc = clamp_nan(__ldcs(x + q), a, b);
-        // upper bound: first knot > x, over [0, N+1), clamped to [1, N]
-        int lo = 0, hi = N + 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_kv[mid].x > xc) hi = mid; else lo = mid + 1;
+    if constexpr (SYNTH)
+        cta_sum_to(synth_sum(f, io.seed, a, __fsub_rn(b, a), io.m), s_red, io.sum);
+    else
+        stream_body<float, kVarUnroll>(io.head, io.nvec, f, io.x, io.y, io.m);
+}
+
+// Algorithm 1 with the search of Section IV.  The knots and values sit in
+// shared memory as (x_j, v_j), padded to 2^L entries with (+inf, v_N),
+// 2^L >= N + 1.  The search is unrolled at compile time for that size: L
+// steps, each a shared load, a compare and a select (the ternary operator),
+// so every query runs the same instructions.  After it, j is the largest
+// index with x_j <= x (x clamped to [x_0, x_N]); the interval is i = j + 1,
+// or N at x = x_N.  Step 2 divides; step 3 is the two-product lerp (TEX:
+// the texture filter at i - 1 + delta + 1/2 instead).  NaN compares false
+// everywhere, lands in interval 1 and gives NaN.
+template <int L, bool TEX>
+struct SearchLerp {
+    const float2* s_kv;
+    cudaTextureObject_t tex;
+    float a, b;
+    int N;
+    __device__ __forceinline__ float operator()(float x) const
+    {
+        const float xc = clamp_nan(x, a, b);
+        int j = 0;
+#pragma unroll
+        for (int k = L - 1; k >= 0; --k) {
+            const int t = j + (1 << k);
+            j = (s_kv[t].x <= xc) ? t : j;
         }
-        const int i = min(max(lo, 1), N);
+        const int i = min(j + 1, N);
         const float2 l = s_kv[i - 1], r = s_kv[i];
         const float delta = (xc - l.x) / (r.x - l.x);
-        __stcs(y + q, (1.0f - delta) * l.y + delta * r.y);
+        if constexpr (TEX) {
+            const float yv = tex1D<float>(tex, (float)(i - 1) + delta + 0.5f);
+            return xc != xc ? xc : yv;
+        } else {
+            return (1.0f - delta) * l.y + delta * r.y;
+        }
     }
+};
+
+template <int L, bool TEX, bool SYNTH>
+__global__ void __launch_bounds__(1024) search_kernel(const float* __restrict__ xk_g, const float* __restrict__ vk_g,
+                                                      int N, cudaTextureObject_t tex, const StreamIO io)
+{
+    extern __shared__ float2 s_kv[];
+    const float inf = __int_as_float(0x7f800000);
+    const float vN = vk_g[N];
+    for (int j = threadIdx.x; j < (1 << L); j += blockDim.x)
+        s_kv[j] = j <= N ? make_float2(xk_g[j], vk_g[j]) : make_float2(inf, vN);
+    __syncthreads();
+    const SearchLerp<L, TEX> f{s_kv, tex, s_kv[0].x, s_kv[N].x, N};
+    run_variant<SYNTH>(io, f, f.a, f.b, reinterpret_cast<float*>(s_kv));
 }
 
-// ---- mode 1: interval lookup, then the texture unit's linear filter -------
+// the largest search depth: 2^14 knot slots of 8 bytes fill 128 KB
+constexpr int kMaxSearchLog = 14;
+
+template <bool TEX, bool SYNTH>
+struct SearchTable {
+    using Kern = void (*)(const float*, const float*, int, cudaTextureObject_t, const StreamIO);
+    template <int L>
+    static Kern pick(int l)
+    {
+        if constexpr (L > kMaxSearchLog) {
+            return nullptr;
+        } else {
+            return l == L ? search_kernel<L, TEX, SYNTH> : pick<L + 1>(l);
+        }
+    }
+};
+
+// Mode 1: the interval from the 16-byte (backward-form) index, then the
+// texture filter.
 struct TexArgs {
     const float4* rec;  // backward records
     const TableHeader* hdr;
@@ -363,20 +322,15 @@ struct TexArgs {
     float a, b, inv_w, off;
 };
 
-__global__ void __launch_bounds__(1024) eval_tex_kernel(const TexArgs p, cudaTextureObject_t tex, const float* x,
-                                                        float* y, int64_t m)
-{
-    extern __shared__ float4 s_dyn[];
-    float4* srec = s_dyn;                                        // backward-form records
-    float* s_ih = reinterpret_cast<float*>(s_dyn + p.n_smem);    // N+2 reciprocal lengths
-    const int max_chain = p.hdr->max_chain_b;
-    const int n_stage = min(p.K + p.hdr->n_chain_b, p.n_smem);
-    for (int i = threadIdx.x; i < n_stage; i += blockDim.x) srec[i] = __ldg(p.rec + i);
-    for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) s_ih[i] = p.inv_h[i];
-    __syncthreads();
-    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += nthr) {
-        const float xc = clamp_nan(__ldcs(x + q), p.a, p.b);
+struct TexLerp {
+    const float4* srec;
+    const float* s_ih;
+    cudaTextureObject_t tex;
+    const TexArgs& p;
+    int n_stage, max_chain;
+    __device__ __forceinline__ float operator()(float x) const
+    {
+        const float xc = clamp_nan(x, p.a, p.b);
         const int c = cell_of(xc, p.inv_w, p.off, p.K);
         float4 r = (c < n_stage) ? srec[c] : __ldg(p.rec + c);
         for (int g = 0; g < max_chain && xc >= r.x && is_link(r.w); ++g) {
@@ -394,10 +348,43 @@ __global__ void __launch_bounds__(1024) eval_tex_kernel(const TexArgs p, cudaTex
         } else {
             u = (float)p.N + 0.5f;
         }
-        float yv = tex1D<float>(tex, u);
-        if (xc != xc) yv = xc;
-        __stcs(y + q, yv);
+        const float yv = tex1D<float>(tex, u);
+        return xc != xc ? xc : yv;
     }
+};
+
+template <bool SYNTH>
+__global__ void __launch_bounds__(1024) eval_tex_kernel(const TexArgs p, cudaTextureObject_t tex, const StreamIO io)
+{
+    extern __shared__ float4 s_dyn[];
+    float4* srec = s_dyn;                                        // backward-form records
+    float* s_ih = reinterpret_cast<float*>(s_dyn + p.n_smem);    // N+2 reciprocal lengths
+    const int n_stage = min(p.K + p.hdr->n_chain_b, p.n_smem);
+    for (int i = threadIdx.x; i < n_stage; i += blockDim.x) srec[i] = __ldg(p.rec + i);
+    for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) s_ih[i] = p.inv_h[i];
+    __syncthreads();
+    const TexLerp f{srec, s_ih, tex, p, n_stage, p.hdr->max_chain_b};
+    run_variant<SYNTH>(io, f, p.a, p.b, reinterpret_cast<float*>(s_dyn));
+}
+
+// Mode 5: a uniform partition needs no search (Section IV): the texture
+// coordinate is (x - x_0) N / (x_N - x_0) + 1/2, i.e. i - 1 + delta + 1/2.
+struct UniformTex {
+    cudaTextureObject_t tex;
+    float a, b, scale;  // scale = N / (x_N - x_0)
+    __device__ __forceinline__ float operator()(float x) const
+    {
+        const float xc = clamp_nan(x, a, b);
+        const float yv = tex1D<float>(tex, __fmaf_rn(xc - a, scale, 0.5f));
+        return xc != xc ? xc : yv;
+    }
+};
+
+template <bool SYNTH>
+__global__ void __launch_bounds__(1024) eval_utex_kernel(const UniformTex f, const StreamIO io)
+{
+    __shared__ float s_red[32];
+    run_variant<SYNTH>(io, f, f.a, f.b, s_red);
 }
 
 pwl_status check_common(pwl_table t, const void* x, const void* y, int64_t m)
@@ -440,15 +427,7 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
         smem = eval16_smem_bytes(t);
         if (p.n_smem < p.K) return fail(PWL_ENOTSUP, "16-byte index of %d cells does not fit one CTA", p.K);
     }
-    const uintptr_t ax = reinterpret_cast<uintptr_t>(x), ay = reinterpret_cast<uintptr_t>(y);
-    if ((ax % 16) == (ay % 16) && (ax % sizeof(IO)) == 0) {
-        const int64_t head = std::min<int64_t>(m, (int64_t)(((16 - ax % 16) % 16) / sizeof(IO)));
-        p.head = head;
-        p.nvec = (m - head) / Vec<IO>::n;
-    } else {
-        p.head = 0;
-        p.nvec = 0;
-    }
+    stream_split<IO>(x, y, m, &p.head, &p.nvec);
     const DeviceInfo& di = device_info();
     if (smem > di.smem_optin) return fail(PWL_ENOTSUP, "forward index of %zu bytes does not fit one CTA", smem);
     const bool two = di.smem_per_sm >= 2 * (smem + 1024);
@@ -463,17 +442,13 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
     // but one per SM while each gets a few vectors per warp (the CTAs stage
     // the index concurrently, so spreading costs no latency and uses every
     // SM's loads); tiny ones do not stage the index in idle CTAs
-    const int64_t units = p.nvec + (m - p.nvec * Vec<IO>::n);
-    const int64_t per_cta = (int64_t)1024 * kUnroll;
-    const int64_t spread = std::min<int64_t>(device_info().sms, (units + 255) / 256);
-    const int grid =
-        (int)std::min<int64_t>(max_grid, std::max<int64_t>(1, std::max<int64_t>(spread, (units + per_cta - 1) / per_cta)));
+    const int grid = stream_grid(max_grid, p.nvec + (m - p.nvec * Vec<IO>::n), 1024, kUnroll);
     kern<<<grid, 1024, smem, s>>>(p, x, y, m);
     PWL_CHECK_LAUNCH("eval_kernel");
     return PWL_OK;
 }
 
-pwl_status launch_synth(pwl_table t, uint32_t seed, int64_t m, double* sum, cudaStream_t s)
+pwl_status launch_synth(pwl_table t, int layout, uint32_t seed, int64_t m, double* sum, cudaStream_t s)
 {
     EvalArgs p{};
     p.recP = t->recP;
@@ -485,7 +460,7 @@ pwl_status launch_synth(pwl_table t, uint32_t seed, int64_t m, double* sum, cuda
     p.a = t->a;
     p.b = t->b;
     size_t smem;
-    if (t->layout == 0) {
+    if (layout == 0) {
         p.K = (int)t->K;
         p.s_staged = forward_side_staged(t->N) ? 1 : 0;
         p.inv_w = t->inv_w;
@@ -504,7 +479,7 @@ pwl_status launch_synth(pwl_table t, uint32_t seed, int64_t m, double* sum, cuda
     if (smem > di.smem_optin) return fail(PWL_ENOTSUP, "forward index of %zu bytes does not fit one CTA", smem);
     const bool two = di.smem_per_sm >= 2 * (smem + 1024);
     void (*kern)(const EvalArgs, uint32_t, int64_t, double*);
-    if (t->layout == 0)
+    if (layout == 0)
         kern = two ? eval_synth_kernel<0, 2> : eval_synth_kernel<0, 1>;
     else
         kern = two ? eval_synth_kernel<1, 2> : eval_synth_kernel<1, 1>;
@@ -536,7 +511,7 @@ pwl_status ensure_texture(pwl_table t, cudaStream_t s)
         return fail(PWL_ENOTSUP, "texture path supports at most %d knots", maxa);
     const bool half_texels = (t->dtype == PWL_FP16);
     cudaChannelFormatDesc cd = half_texels ? cudaCreateChannelDescHalf() : cudaCreateChannelDesc<float>();
-    PWL_CUDA_TRY(cudaMallocArray(&t->tex_array, &cd, (size_t)t->N + 1, 0));
+    PWL_CUDA_TRY(dev_malloc_array(&t->tex_array, &cd, (size_t)t->N + 1));
     // from here on a failure frees the array, so that a later call starts afresh
     auto undo = [&](pwl_status st) {
         cudaFreeArray(t->tex_array);
@@ -567,6 +542,70 @@ pwl_status refresh_texture(pwl_table t, cudaStream_t s)
 {
     return t->tex ? copy_texels(t, s) : PWL_OK;
 }
+
+namespace {
+
+// Modes 0, 1, 4 and 5 on a query stream (synth = false: io.x, io.y, io.m)
+// or on generated queries (synth = true: io.seed, io.m, io.sum).
+pwl_status launch_variant(pwl_table t, int mode, bool synth, StreamIO io, cudaStream_t s)
+{
+    const DeviceInfo& di = device_info();
+    if (!synth) stream_split<float>(io.x, io.y, io.m, &io.head, &io.nvec);
+    const int64_t units = synth ? (io.m + 3) / 4 : io.nvec + (io.m - io.nvec * 4);
+    if (mode == 1 || mode == 4 || mode == 5) {
+        pwl_status st = ensure_texture(t, s);
+        if (st != PWL_OK) return st;
+    }
+    int max_grid = 0;
+    if (mode == 0 || mode == 4) {
+        int L = 1;
+        while (((int64_t)1 << L) < t->N + 1) ++L;
+        if (L > kMaxSearchLog)
+            return fail(PWL_ENOTSUP, "search path stages at most 2^%d knots (N = %lld)", kMaxSearchLog,
+                        (long long)t->N);
+        void (*kern)(const float*, const float*, int, cudaTextureObject_t, const StreamIO);
+        if (mode == 0)
+            kern = synth ? SearchTable<false, true>::pick<1>(L) : SearchTable<false, false>::pick<1>(L);
+        else
+            kern = synth ? SearchTable<true, true>::pick<1>(L) : SearchTable<true, false>::pick<1>(L);
+        const size_t smem = std::max<size_t>(sizeof(float2) << L, 128);
+        PWL_CUDA_TRY(occupancy_grid(kern, 1024, smem, &max_grid));
+        kern<<<stream_grid(max_grid, units, 1024, kVarUnroll), 1024, smem, s>>>(t->xk, t->vk, (int)t->N, t->tex, io);
+        PWL_CHECK_LAUNCH("search_kernel");
+        return PWL_OK;
+    }
+    if (mode == 5) {
+        void (*kern)(const UniformTex, const StreamIO) = synth ? eval_utex_kernel<true> : eval_utex_kernel<false>;
+        const UniformTex f{t->tex, t->a, t->b, (float)((double)t->N / ((double)t->b - (double)t->a))};
+        PWL_CUDA_TRY(occupancy_grid(kern, 1024, 0, &max_grid));
+        kern<<<stream_grid(max_grid, units, 1024, kVarUnroll), 1024, 0, s>>>(f, io);
+        PWL_CHECK_LAUNCH("eval_utex_kernel");
+        return PWL_OK;
+    }
+    // mode 1
+    const size_t fixed = sizeof(float) * (size_t)(t->N + 2);
+    if (fixed + 1024 > di.smem_optin) return fail(PWL_ENOTSUP, "table too large for the texture path");
+    TexArgs p{};
+    p.rec = t->rec_b;
+    p.hdr = t->hdr;
+    p.inv_h = t->inv_h;
+    p.K = (int)t->Kb;
+    p.N = (int)t->N;
+    p.n_smem = (int)std::min<int64_t>(t->Kb + t->chain_reserve_b, (int64_t)((di.smem_optin - fixed) / 16));
+    p.a = t->a;
+    p.b = t->b;
+    p.inv_w = t->inv_w_b;
+    p.off = t->off_b;
+    const size_t smem = std::max<size_t>(16 * (size_t)p.n_smem + fixed, 128);
+    void (*kern)(const TexArgs, cudaTextureObject_t, const StreamIO) =
+        synth ? eval_tex_kernel<true> : eval_tex_kernel<false>;
+    PWL_CUDA_TRY(occupancy_grid(kern, 1024, smem, &max_grid));
+    kern<<<stream_grid(max_grid, units, 1024, kVarUnroll), 1024, smem, s>>>(p, t->tex, io);
+    PWL_CHECK_LAUNCH("eval_tex_kernel");
+    return PWL_OK;
+}
+
+}  // namespace
 
 }  // namespace pwl
 
@@ -603,7 +642,27 @@ pwl_status pwl_eval_synthetic(pwl_table t, uint32_t seed, int64_t m, double* d_s
     cudaGetDevice(&dev);
     if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
     if (m == 0) return PWL_OK;
-    return launch_synth(t, seed, m, d_sum, as_stream(stream));
+    return launch_synth(t, t->layout, seed, m, d_sum, as_stream(stream));
+}
+
+pwl_status pwl_eval_synthetic_variant(pwl_table t, int32_t mode, uint32_t seed, int64_t m, double* d_sum,
+                                      void* stream)
+{
+    clear_error();
+    if (!t) return fail(PWL_EINVAL, "table is NULL");
+    if (mode < 0 || mode > 5) return fail(PWL_EINVAL, "unknown mode %d", mode);
+    if (m < 0 || m > ((int64_t)1 << 32)) return fail(PWL_EINVAL, "m must be in [0, 2^32]");
+    if (!d_sum) return fail(PWL_EINVAL, "d_sum is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
+    if (m == 0) return PWL_OK;
+    if (mode == 2 || mode == 3) return launch_synth(t, mode - 2, seed, m, d_sum, as_stream(stream));
+    StreamIO io{};
+    io.m = m;
+    io.seed = seed;
+    io.sum = d_sum;
+    return launch_variant(t, mode, true, io, as_stream(stream));
 }
 
 pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* d_y, int64_t m,
@@ -612,42 +671,15 @@ pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* 
     clear_error();
     pwl_status st = check_common(t, d_x, d_y, m);
     if (st != PWL_OK) return st;
-    if (mode < 0 || mode > 3) return fail(PWL_EINVAL, "unknown mode %d", mode);
+    if (mode < 0 || mode > 5) return fail(PWL_EINVAL, "unknown mode %d", mode);
     if (m == 0) return PWL_OK;
     cudaStream_t s = as_stream(stream);
-    const DeviceInfo& di = device_info();
-    if (mode >= 2) return launch_eval<float>(t, mode - 2, d_x, d_y, m, s);
-    if (mode == 0) {
-        const size_t smem = sizeof(float2) * (size_t)(t->N + 1);
-        if (smem > di.smem_optin)
-            return fail(PWL_ENOTSUP, "binary-search path stages N+1 <= %zu knots", di.smem_optin / 8);
-        int grid = 0;
-        PWL_CUDA_TRY(occupancy_grid(eval_search_kernel, 1024, smem, &grid));
-        eval_search_kernel<<<grid, 1024, smem, s>>>(t->xk, t->vk, (int)t->N, d_x, d_y, m);
-        PWL_CHECK_LAUNCH("eval_search_kernel");
-        return PWL_OK;
-    }
-    st = ensure_texture(t, s);
-    if (st != PWL_OK) return st;
-    const size_t fixed = sizeof(float) * (size_t)(t->N + 2);
-    if (fixed + 1024 > di.smem_optin) return fail(PWL_ENOTSUP, "table too large for the texture path");
-    TexArgs p{};
-    p.rec = t->rec_b;
-    p.hdr = t->hdr;
-    p.inv_h = t->inv_h;
-    p.K = (int)t->Kb;
-    p.N = (int)t->N;
-    p.n_smem = (int)std::min<int64_t>(t->Kb + t->chain_reserve_b, (int64_t)((di.smem_optin - fixed) / 16));
-    p.a = t->a;
-    p.b = t->b;
-    p.inv_w = t->inv_w_b;
-    p.off = t->off_b;
-    const size_t smem = 16 * (size_t)p.n_smem + fixed;
-    int grid = 0;
-    PWL_CUDA_TRY(occupancy_grid(eval_tex_kernel, 1024, smem, &grid));
-    eval_tex_kernel<<<grid, 1024, smem, s>>>(p, t->tex, d_x, d_y, m);
-    PWL_CHECK_LAUNCH("eval_tex_kernel");
-    return PWL_OK;
+    if (mode == 2 || mode == 3) return launch_eval<float>(t, mode - 2, d_x, d_y, m, s);
+    StreamIO io{};
+    io.x = d_x;
+    io.y = d_y;
+    io.m = m;
+    return launch_variant(t, mode, false, io, s);
 }
 
 }  // extern "C"

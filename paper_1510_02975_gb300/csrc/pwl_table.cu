@@ -385,7 +385,7 @@ pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_
     const size_t o_cj = o_vs + align256(4 * n1);
     const size_t o_cp = o_cj + align256(4 * n1);
     const size_t total = o_cp + align256(4 * n1);
-    cudaError_t e = cudaMalloc(&t->buf_base, total);
+    cudaError_t e = dev_malloc(&t->buf_base, total);
     if (e != cudaSuccess) {
         delete t;
         return cuda_fail(e, "cudaMalloc(table)");
@@ -425,7 +425,7 @@ pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_
     const size_t bytes_b = align256(sizeof(float4) * ((size_t)t->Kb + n1));
     const size_t bytes_p = align256(sizeof(float2) * (size_t)t->K);
     const size_t bytes_s = align256(sizeof(float2) * 2 * n1);
-    if ((e = cudaMalloc(&t->buf_rec, 2 * bytes_b + bytes_p + bytes_s)) != cudaSuccess)
+    if ((e = dev_malloc(&t->buf_rec, 2 * bytes_b + bytes_p + bytes_s)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMalloc(records)"));
     char* r = static_cast<char*>(t->buf_rec);
     t->rec_b = reinterpret_cast<float4*>(r);

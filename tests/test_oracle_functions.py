@@ -92,3 +92,33 @@ def test_j0_second_derivative_at_origin():
     desc = {"kind": "bessel_j0", "a": 0.0, "b": 1.0, "p": [1.3, 2.0]}
     assert oracle.f2(desc, [0.0])[0] == pytest.approx(-1.3 * 4.0 / 2.0, rel=1e-15)
     assert oracle.f2(desc, [1e-9])[0] == pytest.approx(-1.3 * 4.0 / 2.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("desc", FUNCS[:6], ids=lambda d: d["kind"])
+def test_f_many_matches_library(desc):
+    x = np.linspace(desc["a"], desc["b"], 1001)
+    assert np.allclose(oracle.f_many(desc, x), _lib_f(desc, x), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("A,alpha", [(1.0, 1.0), (2.0, 0.5), (0.3, 3.7)])
+def test_j0_one_term_is_the_leading_term_of_hankels_expansion(A, alpha):
+    # J0(z) = sqrt(2/(pi z)) [cos w (1 - 9/(128 z^2) + ...) + sin w / (8 z) - ...],
+    # w = z - pi/4 (DLMF 10.17.3 with a_1(0) = -1/8, a_2(0) = 9/128,
+    # a_3(0) = -225/3072); for real z > 0 the remainder after a term is
+    # bounded by the next term (DLMF 10.17(iii)).  So J0 minus the oracle's
+    # one-term form, minus the 1/(8z) sine term, is within the 9/(128 z^2)
+    # and 225/(3072 z^3) terms: a wrong phase, sign or amplitude fails.
+    sc = pytest.importorskip("scipy.special")
+    desc = {"kind": "bessel_j0", "a": 0.0, "b": 100.0, "p": [A, alpha]}
+    z = np.linspace(8.0, 400.0, 20001)
+    x = z / alpha
+    s = np.sqrt(2.0 / (np.pi * z))
+    w = z - np.pi / 4
+    one = oracle.j0_one_term(desc, x)
+    rest = A * sc.j0(z) - one - A * s * np.sin(w) / (8 * z)
+    # (+ the rounding of z = alpha (z / alpha) inside the oracle: ~ulp(z))
+    bound = A * s * (9.0 / (128 * z**2) + 225.0 / (3072 * z**3)) + 4e-16 * A * z
+    assert np.all(np.abs(rest) <= bound)
+    # and the one-term form is not J0 itself: its error is the 1/(8z) term
+    err = np.abs(A * sc.j0(z) - one)
+    assert np.max(err / (A * s / (8 * z))) > 0.9
