@@ -54,8 +54,11 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-log2", type=int, default=21, help="oracle queries per (table, set)")
+    ap.add_argument("--cpu-sample-log2", type=int, default=24,
+                    help="queries per function of the single-thread oracle timing (log2)")
     ap.add_argument("--fwd-bwd-steps", type=int, default=3)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the precision, Table I, channel-wise and batched measurements of the default line")
     ap.add_argument("--report", default=None, choices=[None, "variants", "channels", "batched", "backward"],
                     help="variants: per-table throughput of every evaluation path and the error of each "
                          "vertex-table precision (one JSON line)")
@@ -294,6 +297,15 @@ class Workload:
                     else:
                         pwl.pwl_eval(t.handle, self.x[(fi, qs)], self.y)
 
+    def launch_keys(self):
+        """Names of a step's evaluation launches, in launch order."""
+        keys = []
+        for fi, N, kn, vi, vp, wsd, wsp, ti, tp in self.items:
+            for form in FORMS:
+                for qs in ("uniform", "normal"):
+                    keys.append(f"{FUNC_NAMES[fi]}/{form}/N{N}/{qs}")
+        return keys
+
     def error_report(self, sample=1 << 20):
         """max |y - f| (FP64 f) and max |y - v64| (FP64 PWL) on a sample of
         each query set, per function and form, at N = 4096."""
@@ -349,6 +361,10 @@ def run_ours(args):
     value, ms_max = replica_throughput(dist, ms, wl.evals_per_step, args.steps)
     launch_ms = [a.elapsed_time(b) for a, b in events]
     avg_launch_s = float(np.mean(launch_ms)) / 1e3
+    per_table = {}
+    for k, ms_k in zip(wl.launch_keys() * args.steps, launch_ms):
+        per_table.setdefault(k, []).append(ms_k)
+    per_table_gbs = {k: round(BYTES_FWD * wl.m / (float(np.mean(v)) / 1e3) / 1e9, 1) for k, v in per_table.items()}
     peak, peak_kind = measured_peaks()
     achieved = BYTES_FWD * wl.m / avg_launch_s / 1e9
 
@@ -368,10 +384,16 @@ def run_ours(args):
     errors = wl.error_report()
     ceiling = compute_ceiling(wl)
     small = small_case(wl)
+    extra = {}
+    if not args.no_configs:
+        extra["precision"] = precision_measure(wl)
+        extra["table_I"] = table_one_measure(wl)
+        extra["channels"] = channels_measure()
+        extra["batched"] = batched_measure(steps=3)
     e2e = None if args.no_e2e else run_e2e(wl, args.e2e_steps)
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.cpu_sample_log2)
+        cpu = cpu_baseline(wl, args.cpu_sample_log2)
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -408,12 +430,14 @@ def run_ours(args):
             "launches_timed": len(launch_ms),
         },
         "design_ms_per_step": round(design_ms, 3),
+        "per_table_forward_gbs": per_table_gbs,
         "fwd_bwd": fb,
         "errors_N4096": errors,
         "compute_ceiling": ceiling,
         "small_case": small,
         "gpu_launches": gpu_launches_per_step(wl) * args.steps,
         "clocks": clk,
+        **extra,
     }
     if e2e is not None:
         line["e2e"] = e2e
@@ -438,6 +462,109 @@ def compute_ceiling(wl, m: int = 1 << 28, reps: int = 5):
         out[f"gaussian/project/N{N}"] = {"ps_per_eval": round(sec / m * 1e12, 3),
                                          "G_evals_per_s": round(m / sec / 1e9, 1)}
     return out
+
+
+def precision_measure(wl, N: int = 1024, reps: int = 3, sample: int = 1 << 20) -> dict:
+    """Vertex tables in FP32 / BF16 / FP16 with the FP32 FMA lerp (pwl_eval)
+    and with the texture filter (fixed-point weight; FP32 texels, FP16 for
+    FP16 tables), at N = 1024 on the 2^28 uniform query set of each function
+    (P_T values): throughput and fraction of the measured copy bandwidth,
+    and max / RMS error against FP64 f and against the FP64 CPWL function
+    (on the first 2^20 queries)."""
+    torch, pwl = wl.torch, wl.pwl
+    peak, _ = measured_peaks()
+    out = {}
+    for fi, n, kn, vi, vp, wsd, wsp, ti, tp in wl.items:
+        if n != N:
+            continue
+        name = FUNC_NAMES[fi]
+        x = wl.x[(fi, "uniform")]
+        xs = x[:sample]
+        xh = xs.cpu().numpy().astype(np.float64)
+        fx = f64(name, xh)
+        k64, v64 = kn.cpu().numpy(), vp.cpu().numpy()
+        pw = np.interp(xh, k64, v64)
+        for dt in ("fp32", "bf16", "fp16"):
+            t = pwl.Table(kn, vp, dt)
+            for lerp, mode_fn in (("fma", lambda xx, yy: pwl.pwl_eval(t.handle, xx, yy)),
+                                  ("texture", lambda xx, yy: pwl.pwl_eval_variant(t.handle, 1, xx, yy))):
+                sec = time_launches(lambda: mode_fn(x, wl.y), reps)
+                gbs = BYTES_FWD * wl.m / sec / 1e9
+                yv = mode_fn(xs, torch.empty_like(xs)).cpu().numpy().astype(np.float64)
+                ef, ep = yv - fx, yv - pw
+                out[f"{name}/{dt}/{lerp}"] = {
+                    "gbs": round(gbs, 1), "frac_of_peak": round(gbs / peak, 4),
+                    "max_err_vs_f64_f": float(np.abs(ef).max()), "rms_err_vs_f64_f": float(np.sqrt(np.mean(ef * ef))),
+                    "max_err_vs_f64_pwl": float(np.abs(ep).max()),
+                    "rms_err_vs_f64_pwl": float(np.sqrt(np.mean(ep * ep)))}
+            t.close()
+    return {"N": N, "form": "project", "queries": wl.m, "error_sample": sample, "results": out}
+
+
+# The paper's Table I (GTX 580, ps per evaluation, Gaussian), for context
+PAPER_TABLE_I_PS = {
+    "expf": 33.3, "__expf": 14.2, "uniform_manual": 19.75, "uniform_texture": 7.85,
+    "optimized_manual": {"32": 142.0, "64": 161.9, "128": 181.8, "256": 203.1, "512": 224.1},
+    "optimized_texture": {"32": 122.7, "64": 142.9, "128": 163.2, "256": 188.3, "512": 211.1},
+    "lorentzian_division": 19.5, "lorentzian_fast_division": 9.2, "j0_cuda": 78.0, "j0_asymptotic_sfu": 42.0,
+}
+
+
+def table_one_measure(wl, m: int = 1 << 28, reps: int = 3) -> dict:
+    """Table I on this GPU: ps per evaluation with queries generated in
+    registers (no memory traffic; the paper's synthetic benchmark) for every
+    row: the direct Gaussian with expf and __expf, the uniform partition
+    (cell lookup with the FMA lerp; texture coordinate straight from x), the
+    nearly optimal partition with the paper's unrolled binary search (FMA
+    lerp; texture filter) and with this library's cell index (FMA; texture),
+    at N + 1 = 32 .. 512 knots of the Gaussian on [-4, 4] (P_T values); plus
+    the direct Lorentzian (IEEE and fast division) and J0 (j0f; the one-term
+    asymptotic form with SFU cos and rsqrt).  Then the same direct kernels
+    streaming 2^28 FP32 queries from HBM (GB/s, 8 bytes per query)."""
+    torch, pwl, W = wl.torch, wl.pwl, wl.W
+    acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ps = lambda sec: round(sec / m * 1e12, 3)
+    gauss, lor = W.PAPER_FUNCTIONS["gaussian"], W.PAPER_FUNCTIONS["lorentzian"]
+    j0 = W.PAPER_FUNCTIONS["bessel_j0"]
+    rows = {}
+    for key, f, meth in (("expf", gauss, "library"), ("__expf", gauss, "fast"),
+                         ("lorentzian_division", lor, "library"), ("lorentzian_fast_division", lor, "fast"),
+                         ("j0_cuda", j0, "library"), ("j0_asymptotic_sfu", j0, "fast")):
+        rows[key] = ps(time_launches(lambda: pwl.pwl_direct_synthetic(f, meth, m, 11, acc), reps))
+    cols = {k: {} for k in ("uniform_manual", "uniform_texture", "optimized_search_manual",
+                            "optimized_search_texture", "optimized_cells_manual", "optimized_cells_texture")}
+    a, b = gauss["a"], gauss["b"]
+    for knots in (32, 64, 128, 256, 512):
+        n = knots - 1
+        ku = torch.tensor(a + (b - a) * np.arange(n + 1) / n, dtype=torch.float64, device="cuda")
+        ku[-1] = b
+        tu = pwl.Table(ku, pwl.pwl_project(gauss, ku, "project"), "fp32", 2 * n)
+        ko = pwl.pwl_design(gauss, n)
+        to = pwl.Table(ko, pwl.pwl_project(gauss, ko, "project"))
+        for key, t, mode in (("uniform_manual", tu, None), ("uniform_texture", tu, 5),
+                             ("optimized_search_manual", to, 0), ("optimized_search_texture", to, 4),
+                             ("optimized_cells_manual", to, None), ("optimized_cells_texture", to, 1)):
+            if mode is None:
+                fn = lambda: pwl.pwl_eval_synthetic(t.handle, m, 11, acc)
+            else:
+                fn = lambda: pwl.pwl_eval_synthetic_variant(t.handle, mode, m, 11, acc)
+            cols[key][str(knots)] = ps(time_launches(fn, reps))
+        tu.close()
+        to.close()
+    rows.update(cols)
+    peak, _ = measured_peaks()
+    stream = {}
+    for key, fi, meth in (("expf", 0, "library"), ("__expf", 0, "fast"), ("lorentzian_division", 1, "library"),
+                          ("lorentzian_fast_division", 1, "fast"), ("j0_cuda", 2, "library"),
+                          ("j0_asymptotic_sfu", 2, "fast")):
+        f = W.PAPER_FUNCTIONS[FUNC_NAMES[fi]]
+        x = wl.x[(fi, "uniform")]
+        sec = time_launches(lambda: pwl.pwl_direct_eval(f, meth, x, wl.y), reps)
+        gbs = BYTES_FWD * wl.m / sec / 1e9
+        stream[key] = {"gbs": round(gbs, 1), "frac_of_peak": round(gbs / peak, 4),
+                       "G_evals_per_s": round(wl.m / sec / 1e9, 1)}
+    return {"queries": m, "ps_per_eval_register_generated": rows, "direct_streaming_2e28": stream,
+            "paper_gtx580_ps": PAPER_TABLE_I_PS}
 
 
 def small_case(wl, reps: int = 50):
@@ -518,9 +645,22 @@ def fwd_bwd(wl, steps):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     evals = len(bufs) * 2 * wl.m * steps
+    # the backward calls alone, per table size and query set (CUDA events
+    # around each call: the backward kernel and its row reduction)
+    bwd = {}
+    for fi, t, gv, gk, ws in bufs:
+        N = int(t.info["n_intervals"])
+        for qs in ("uniform", "normal"):
+            x = wl.x[(fi, qs)]
+            sec = time_launches(lambda: pwl.pwl_eval_backward(t.handle, x, gy, gx, gv, gk, ws), 2)
+            bwd.setdefault(f"N{N}/{qs}", []).append(sec)
+    peak, _ = measured_peaks()
+    by_n = {k: {"gbs": round(BYTES_BWD * wl.m / float(np.mean(v)) / 1e9, 1),
+                "frac_of_peak": round(BYTES_BWD * wl.m / float(np.mean(v)) / 1e9 / peak, 4)} for k, v in bwd.items()}
+    gbs = evals * (BYTES_FWD + BYTES_BWD) / (ms / 1e3) / 1e9
     return {"value": round(evals / (ms / 1e3) / 1e9, 3), "unit": "G evals/s (forward + backward)",
-            "bytes_per_eval": BYTES_FWD + BYTES_BWD,
-            "gbs": round(evals * (BYTES_FWD + BYTES_BWD) / (ms / 1e3) / 1e9, 1)}
+            "bytes_per_eval": BYTES_FWD + BYTES_BWD, "gbs": round(gbs, 1), "frac_of_peak": round(gbs / peak, 4),
+            "backward_alone": by_n}
 
 
 def run_e2e(wl, steps):
@@ -588,10 +728,35 @@ def run_e2e(wl, steps):
 # ----------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_step(sample_log2: int, seed_offset: int = 0):
+def host_threads() -> int:
+    """Host CPU threads this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_eval_threads(k, v, x, threads: int) -> np.ndarray:
+    """The oracle's Algorithm 1 over x, split into `threads` contiguous
+    ranges evaluated by as many host threads (the C call releases the GIL)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    y = np.empty_like(x)
+    bounds = np.linspace(0, x.size, threads + 1).astype(np.int64)
+
+    def work(i):
+        y[bounds[i]:bounds[i + 1]] = oracle.evaluate(k, v, x[bounds[i]:bounds[i + 1]])
+
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(work, range(threads)))
+    return y
+
+
+def oracle_step(sample_log2: int, seed_offset: int = 0, threads: int = 1):
     """One bounded sample of the workload on the FP64 CPU oracle: design and
-    both vertex-value forms for all 9 (function, N), then 2^sample_log2
-    queries of each set through each table.  Returns (evals, seconds)."""
+    both vertex-value forms for all 9 (function, N) (one thread), then
+    2^sample_log2 queries of each set through each table (over `threads`
+    host threads).  Returns (evals, seconds)."""
     import oracle
     from paper_1510_02975_gb300 import workloads as W
     rng = np.random.default_rng(1234 + seed_offset)
@@ -607,18 +772,68 @@ def oracle_step(sample_log2: int, seed_offset: int = 0):
             for form in FORMS:
                 v = oracle.values(f, k, form)
                 for xs in (xu, xn):
-                    oracle.evaluate(k, v, xs)
+                    if threads > 1:
+                        oracle_eval_threads(k, v, xs, threads)
+                    else:
+                        oracle.evaluate(k, v, xs)
                     evals += n
     return evals, time.perf_counter() - t0
 
 
-def cpu_baseline(sample_log2: int):
+def cpu_baseline(wl, single_log2: int = 24, n_table: int = 1024):
+    """The FP64 C oracle on this host's CPU cores, on the bench's own query
+    sets (the 2^28 uniform set of each function, copied to the host):
+      - design: the oracle's knots and both vertex-value forms for every
+        (function, N) of the workload, one thread, timed apart;
+      - single thread: Algorithm 1 (binary search + lerp) through the
+        N = 1024 P_T table on the first 2^24 queries of each set;
+      - all cores: the same tables on the full 2^28 queries of each set,
+        split into contiguous ranges, one per host thread.
+    `value` is the all-core evaluation rate."""
     import oracle
+    from paper_1510_02975_gb300 import workloads as W
     oracle.build()
-    evals, sec = oracle_step(sample_log2)
-    return {"value": round(evals / sec / 1e9, 6), "unit": "G evals/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, one thread: design + pi_T + P_T for 3 functions x N in {list(NS)}, "
-                      f"then 2^{sample_log2} queries per (table, query set) = {evals} evaluations in {sec:.1f} s"}
+    threads = host_threads()
+    design = {}
+    tables = {}
+    for name in FUNC_NAMES:
+        f = W.PAPER_FUNCTIONS[name]
+        for N in NS:
+            t0 = time.perf_counter()
+            k = oracle.design(f, N)
+            t1 = time.perf_counter()
+            oracle.values(f, k, "interp")
+            t2 = time.perf_counter()
+            v = oracle.values(f, k, "project")
+            t3 = time.perf_counter()
+            design[f"{name}/N{N}"] = {"design_ms": round((t1 - t0) * 1e3, 2), "interp_ms": round((t2 - t1) * 1e3, 2),
+                                      "project_ms": round((t3 - t2) * 1e3, 2)}
+            if N == n_table:
+                tables[name] = (k, v)
+    st_evals = st_sec = mc_evals = mc_sec = 0.0
+    for fi, name in enumerate(FUNC_NAMES):
+        x = wl.x[(fi, "uniform")].cpu().numpy().astype(np.float64)
+        k, v = tables[name]
+        t0 = time.perf_counter()
+        oracle.evaluate(k, v, x[: 1 << single_log2])
+        st_sec += time.perf_counter() - t0
+        st_evals += 1 << single_log2
+        t0 = time.perf_counter()
+        oracle_eval_threads(k, v, x, threads)
+        mc_sec += time.perf_counter() - t0
+        mc_evals += x.size
+        del x
+    total_design_ms = sum(d["design_ms"] + d["interp_ms"] + d["project_ms"] for d in design.values())
+    return {"value": round(mc_evals / mc_sec / 1e9, 6), "unit": "G evals/s", "cores": threads, "kind": "oracle",
+            "sample": f"FP64 C oracle (binary search + lerp) through the N = {n_table} P_T table of each of the 3 "
+                      f"functions: all {threads} host threads on the full 2^{int(np.log2(wl.m))} uniform set of "
+                      f"each function ({int(mc_evals)} evaluations in {mc_sec:.1f} s, contiguous ranges per thread)",
+            "single_thread": {"value": round(st_evals / st_sec / 1e9, 6), "unit": "G evals/s", "cores": 1,
+                              "sample": f"first 2^{single_log2} queries of each set ({int(st_evals)} evaluations in "
+                                        f"{st_sec:.1f} s)"},
+            "design_one_thread": {"total_ms": round(total_design_ms, 1), "per_table": design,
+                                  "what": "oracle design (density, cumulative, inversion) and both vertex-value "
+                                          "forms per (function, N), M = 64 N, Q = 8"}}
 
 
 def run_reference(args):
@@ -627,12 +842,13 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    sample = 18
+    sample = 20
+    threads = host_threads()
     for w in range(args.warmup):
-        oracle_step(sample, w)
+        oracle_step(sample, w, threads)
     total_e, total_s = 0, 0.0
     for s in range(args.steps):
-        e, sec = oracle_step(sample, 100 + s)
+        e, sec = oracle_step(sample, 100 + s, threads)
         total_e += e
         total_s += sec
     value = total_e / total_s / 1e9
@@ -643,10 +859,11 @@ def run_reference(args):
         "data": "synthetic: seeded uniform and clipped-normal queries; analytic functions",
         "impl": "reference",
         "config": {"workload": "3 functions x N in {256,1024,4096} x {pi_T, P_T}; design + values on the "
-                               f"oracle, then 2^{sample} queries per (table, query set) per step",
+                               f"oracle (one thread), then 2^{sample} queries per (table, query set) per step "
+                               f"over {threads} host threads",
                    "evals_per_step": total_e // max(args.steps, 1)},
-        "cpu_baseline": {"value": round(value, 6), "unit": "G evals/s", "cores": 1, "kind": "oracle",
-                         "sample": f"2^{sample} queries per (table, query set) per step"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "G evals/s", "cores": threads, "kind": "oracle",
+                         "sample": f"2^{sample} queries per (table, query set) per step, design included"},
         "e2e": {"value": round(value, 6), "unit": "G evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -828,18 +1045,16 @@ def run_backward(args):
                       "peak_kind": kind, "tables": out}), flush=True)
 
 
-def run_channels(args):
-    """Channel-wise learnable map: x[65536, 4096] ~ N(0, 2^2) (FP32 and BF16),
+def channels_measure(rows: int = 65536, reps: int = 5) -> dict:
+    """Channel-wise learnable map: x[rows, 4096] ~ N(0, 2^2) (FP32 and BF16),
     4096 channels of 257 knots on [-8, 8] from the Gaussian design and P_T
     values, perturbed per channel; forward, backward (x, values, knots) and
-    fwd+bwd throughput."""
+    fwd+bwd throughput (CUDA events, mean of `reps` calls after a warm-up)."""
     import torch
 
     import paper_1510_02975_gb300 as pwl
-    from paper_1510_02975_gb300 import _build
     from paper_1510_02975_gb300 import workloads as W
-    _build.build()
-    R, C, N = args.rows, 4096, 256
+    R, C, N = rows, 4096, 256
     f = {"kind": "gaussian", "a": -8.0, "b": 8.0, "p": [1.0, 0.0, 1.0]}
     k64 = pwl.pwl_design(f, N)
     v64 = pwl.pwl_project(f, k64, "project")
@@ -858,19 +1073,29 @@ def run_channels(args):
     yb = torch.empty_like(xb)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     m = R * C
-    out = {}
+    peak, kind = measured_peaks()
+    out = {"shape": [R, C], "knots_per_channel": N + 1, "peak_gbs": peak, "peak_kind": kind}
     for label, fn, nbytes in (
             ("forward_fp32", lambda: pwl.pwl_channels_forward(knots, values, x, y, status=st), 8),
             ("forward_bf16", lambda: pwl.pwl_channels_forward(knots, values, xb, yb, status=st), 4),
             ("backward_fp32", lambda: pwl.pwl_channels_backward(knots, values, x, gy, gx, gv, gk, status=st), 12),
             ("fwd_bwd_fp32", lambda: (pwl.pwl_channels_forward(knots, values, x, y, status=st),
                                       pwl.pwl_channels_backward(knots, values, x, gy, gx, gv, gk, status=st)), 20)):
-        sec = time_launches(fn)
-        out[label] = {"G_evals_per_s": round(m / sec / 1e9, 2), "gbs": round(nbytes * m / sec / 1e9, 1),
-                      "ms": round(sec * 1e3, 4), "bytes_per_eval": nbytes}
-    peak, kind = measured_peaks()
-    print(json.dumps({"report": "channels", "shape": [R, C], "knots_per_channel": N + 1, "peak_gbs": peak,
-                      "peak_kind": kind, "status": int(st.item()), "results": out}), flush=True)
+        sec = time_launches(fn, reps)
+        gbs = nbytes * m / sec / 1e9
+        out[label] = {"G_evals_per_s": round(m / sec / 1e9, 2), "gbs": round(gbs, 1),
+                      "frac_of_peak": round(gbs / peak, 4), "ms": round(sec * 1e3, 4), "bytes_per_eval": nbytes}
+    out["status"] = int(st.item())
+    del x, gy, y, gx, xb, yb
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_channels(args):
+    from paper_1510_02975_gb300 import _build
+    _build.build()
+    out = channels_measure(args.rows)
+    print(json.dumps({"report": "channels", **out}), flush=True)
 
 
 def f64_desc(desc, x):
@@ -886,7 +1111,8 @@ def f64_desc(desc, x):
     return p[0] * j0(p[1] * x)
 
 
-def run_batched(args):
+def batched_measure(n_funcs: int = 4096, m_per_interval: int = 16, cells_per_knot: int = 0, steps: int = 5,
+                    per_function: bool = False) -> dict:
     """Batches of independent functions: 4096 functions (Gaussians, sigma
     log-uniform on [0.1, 10]; Lorentzians, gamma log-uniform on [0.1, 10];
     J0(alpha x), alpha uniform on [0.5, 5]), N_f + 1 uniform on 16..4096
@@ -897,14 +1123,12 @@ def run_batched(args):
     import torch
 
     import paper_1510_02975_gb300 as pwl
-    from paper_1510_02975_gb300 import _build
     from paper_1510_02975_gb300 import workloads as W
-    _build.build()
-    funcs, n_int, n_q = W.batch_functions(args.batch_funcs, seed=3)
+    funcs, n_int, n_q = W.batch_functions(n_funcs, seed=3)
     x, qo = W.batch_queries(funcs, n_q, seed=6)
     y = torch.empty_like(x)
     nq = int(qo[-1])
-    b = pwl.Batch(funcs, n_int, m_per_interval=args.batch_m, cells_per_knot=args.batch_cpk)
+    b = pwl.Batch(funcs, n_int, m_per_interval=m_per_interval, cells_per_knot=cells_per_knot)
     prec = "fp32"
 
     def pipeline(stream=None):
@@ -934,12 +1158,12 @@ def run_batched(args):
         "build": time_launches(lambda: b.build()),
         "eval": time_launches(lambda: b.eval(x, y)),
     }
-    step = time_launches(graph.replay, reps=max(args.steps, 3))
+    step = time_launches(graph.replay, reps=max(steps, 3))
     peak, kind = measured_peaks()
     ev_gbs = BYTES_FWD * nq / phases["eval"] / 1e9
     out = {
-        "report": "batched", "n_funcs": len(funcs), "total_knots": int(info["total_knots"]),
-        "total_queries": nq, "m_per_interval": args.batch_m, "cells_per_knot": args.batch_cpk or 3,
+        "n_funcs": len(funcs), "total_knots": int(info["total_knots"]),
+        "total_queries": nq, "m_per_interval": m_per_interval, "cells_per_knot": cells_per_knot or 3,
         "step_ms": round(step * 1e3, 4),
         "step_G_evals_per_s": round(nq / step / 1e9, 2),
         "phase_ms": {k: round(v * 1e3, 4) for k, v in phases.items()},
@@ -963,7 +1187,7 @@ def run_batched(args):
         k = funcs[fi]["kind"]
         err[k] = max(err.get(k, 0.0), e)
     out["max_err_vs_f64_f_first64"] = err
-    if not args.no_per_function:
+    if per_function:
         # the same evaluation as one pwl_eval launch per function (4096
         # tables built from the batch's FP64 knots and values), the launches
         # captured in one CUDA graph
@@ -994,7 +1218,16 @@ def run_batched(args):
         for t in tables:
             t.close()
     b.close()
-    print(json.dumps(out), flush=True)
+    del graph, x, y
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    from paper_1510_02975_gb300 import _build
+    _build.build()
+    out = batched_measure(args.batch_funcs, args.batch_m, args.batch_cpk, args.steps, not args.no_per_function)
+    print(json.dumps({"report": "batched", **out}), flush=True)
 
 
 def main():
