@@ -45,7 +45,7 @@ struct BwdArgs {
     const float* inv_h;
     const float* slope;
     int N, K, n_smem, max_chain;
-    int lanes;          // accumulator copies (1, 8 or 32), lane l adds into copy l mod lanes
+    int lanes;          // accumulator copies (a power of two <= 32), lane l adds into copy l mod lanes
     int rep_shift;      // log2 of the record copies R: lane l reads srec[c R + l mod R]
     float a, b, inv_w, off;
     float s_first, s_last;  // slopes of intervals 1 and N (set by the kernel)
