@@ -59,7 +59,8 @@ def parse_args():
     ap.add_argument("--fwd-bwd-steps", type=int, default=3)
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the precision, Table I, channel-wise and batched measurements of the default line")
-    ap.add_argument("--report", default=None, choices=[None, "variants", "channels", "batched", "backward"],
+    ap.add_argument("--report", default=None,
+                    choices=[None, "variants", "channels", "batched", "backward", "table1"],
                     help="variants: per-table throughput of every evaluation path and the error of each "
                          "vertex-table precision (one JSON line)")
     ap.add_argument("--k-cells", type=int, default=0, help="cell count of the tables in --report variants")
@@ -1003,6 +1004,30 @@ def uniform_vs_optimised(pwl, W, m, y, sizing):
     return out
 
 
+class _Queries:
+    """The uniform query sets of the bench workload only (what table_one_measure reads)."""
+
+    def __init__(self, log2m: int):
+        import torch
+
+        import paper_1510_02975_gb300 as pwl
+        from paper_1510_02975_gb300 import workloads as W
+        self.torch, self.pwl, self.W = torch, pwl, W
+        self.m = 1 << log2m
+        self.x = {(fi, "uniform"): W.uniform_queries(W.PAPER_FUNCTIONS[n], self.m, seed=1)
+                  for fi, n in enumerate(FUNC_NAMES)}
+        self.y = torch.empty(self.m, dtype=torch.float32, device="cuda")
+
+
+def run_table1(args):
+    """Table I on this GPU alone (the `table_I` key of the default line),
+    with 2^log2m queries."""
+    from paper_1510_02975_gb300 import _build
+    _build.build()
+    out = table_one_measure(_Queries(args.log2m), m=1 << args.log2m)
+    print(json.dumps({"report": "table1", **out}), flush=True)
+
+
 def run_backward(args):
     """pwl_eval_backward (x, values, knots) per call on the Gaussian tables at
     N in {256, 1024, 4096} (P_T values), 2^log2m queries, for query sets that
@@ -1243,6 +1268,9 @@ def main():
         return
     if args.report == "backward":
         run_backward(args)
+        return
+    if args.report == "table1":
+        run_table1(args)
         return
     if args.impl == "reference":
         run_reference(args)
