@@ -244,7 +244,9 @@ typedef struct {
     const void* d_values;  /* device, N+1 values in value_dtype */
     size_t eval_smem_bytes;     /* shared memory one forward CTA stages */
     size_t backward_smem_bytes; /* shared memory one backward CTA stages */
-    int32_t layout;             /* forward index pwl_eval uses: 0 = 8-byte, 1 = 16-byte records */
+    int32_t layout;             /* forward index pwl_eval uses: 0 = 8-byte cell records with two
+                                   side records per knot, 1 = 16-byte records, 2 = 8-byte cell
+                                   records with one side record per knot */
     int32_t reserved2;
 } pwl_table_info;
 
@@ -275,6 +277,8 @@ pwl_status pwl_eval(pwl_table t, const void* d_x, void* d_y, int64_t m, int32_t 
  *           bits), so results differ from pwl_eval by up to |v_i - v_{i-1}|/256;
  *   mode 2, 3: pwl_eval forced to its 8-byte or 16-byte cell index (it
  *           otherwise picks one per table, see pwl_table_info.layout);
+ *   mode 6: pwl_eval forced to the 8-byte cell index with one side record
+ *           per knot (layout 2; the same results as mode 2 on the same cells);
  *   mode 4: the search of mode 0, then the texture filter of mode 1 (Table
  *           I's optimized partition with hardware interpolation);
  *   mode 5: the uniform-partition lookup of Section IV with the texture
@@ -299,7 +303,7 @@ pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* 
 pwl_status pwl_eval_synthetic(pwl_table t, uint32_t seed, int64_t m, double* d_sum, void* stream);
 
 /* pwl_eval_synthetic for the comparison paths of pwl_eval_variant (modes
- * 0..5, same queries and checksum): the compute ceilings of Table I's rows
+ * 0..6, same queries and checksum): the compute ceilings of Table I's rows
  * on this GPU (binary search vs cell index, lerp vs texture filter).       */
 pwl_status pwl_eval_synthetic_variant(pwl_table t, int32_t mode, uint32_t seed, int64_t m, double* d_sum,
                                       void* stream);

@@ -444,9 +444,11 @@ struct pwl_table_s {
     int* cpos;         // build scratch: chain slot of every knot
     float2* recP;      // forward, 8-byte layout: K cell records
     float2* recS;      // forward, 8-byte layout: 2 (N+1) side records
+    float2* recS8;     // forward, 8-byte layout with one side record per knot: N+1 records {v_k, s_{k+1}}
     float4* rec16;     // forward, 16-byte layout on the K_b grid: K_b + N + 1 records
     float4* rec_b;     // backward: K_b + N + 1 records
-    int32_t layout;    // forward layout pwl_eval uses: 0 = 8-byte cells, 1 = 16-byte cells
+    int32_t layout;    // forward layout pwl_eval uses: 0 = 8-byte cells, 1 = 16-byte cells,
+                       // 2 = 8-byte cells with one side record per knot
     cudaArray_t tex_array;
     cudaTextureObject_t tex;
 };

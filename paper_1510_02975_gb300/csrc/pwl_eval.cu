@@ -24,6 +24,8 @@
 //   mode 1  interval lookup through the 16-byte index, then the texture
 //           unit's linear filter at i - 1 + delta + 1/2 (Section IV-B)
 //   mode 2, 3  the main path forced to the 8-byte or the 16-byte index
+//   mode 6  the main path forced to the 8-byte index with one side record
+//           per knot
 //   mode 4  the search of mode 0, then the texture filter (the paper's
 //           "optimized partition, hardware interpolation", Table I)
 //   mode 5  uniform partition: no search, the texture coordinate
@@ -46,6 +48,7 @@ constexpr int kUnroll = 4;
 struct EvalArgs {
     const float2* recP;   // 8-byte layout: K cell records
     const float2* recS;   // 8-byte layout: 2 (N+1) side records
+    const float2* recS8;  // 8-byte layout with one side record per knot: N+1 records {v_k, s_{k+1}}
     const float* xk;      // N+1 FP32 knots (chain walks of the 8-byte layout)
     const float4* rec16;  // 16-byte layout: K cell records + chain area
     const TableHeader* hdr;
@@ -77,7 +80,10 @@ __device__ __noinline__ int2 walk_chain8(float xc, int k, float xk, const float*
     return make_int2(k, __float_as_int(xk));
 }
 
-template <bool CHAINS, bool OUTLINE = false>
+// SIDE8: one side record per knot, {v_k, s_{k+1}}; left of x_k the slope is
+// s_k, from the record of knot k - 1 (the same v_k + (x - x_k) s as the two
+// side records give, at half their shared memory).
+template <bool CHAINS, bool OUTLINE = false, bool SIDE8 = false>
 struct Lerp8 {
     const float2* sP;
     const float2* sS;
@@ -109,8 +115,13 @@ struct Lerp8 {
                 }
             }
             // x == x_k takes the right side: v_k + 0 * s is exactly v_k
-            const int si = 2 * k + (xc >= xk ? 1 : 0);
-            q = p.s_staged ? sS[si] : __ldg(p.recS + si);
+            if constexpr (SIDE8) {
+                q = sS[k];
+                if (xc < xk) q.y = sS[k - 1].y;  // left of x_k (k >= 1 there: x >= x_0)
+            } else {
+                const int si = 2 * k + (xc >= xk ? 1 : 0);
+                q = p.s_staged ? sS[si] : __ldg(p.recS + si);
+            }
             anchor = xk;
         }
         return __fmaf_rn(xc - anchor, q.y, q.x);
@@ -145,7 +156,8 @@ __device__ __forceinline__ void eval_body(const EvalArgs& p, const L& f, const I
     stream_body<IO, U>(p.head, p.nvec, f, x, y, m);
 }
 
-// LAYOUT 0: 8-byte index; 1: 16-byte index.  MINB = 2 asks for <= 32
+// LAYOUT 0: 8-byte index; 1: 16-byte index; 2: 8-byte index with one side
+// record per knot.  MINB = 2 asks for <= 32
 // registers so that two 1024-thread CTAs fit an SM (used when two copies of
 // the index fit its shared memory); it keeps two 16-byte vectors in flight
 // per thread instead of four, the same bytes in flight per SM.
@@ -155,21 +167,24 @@ __global__ void __launch_bounds__(1024, MINB) eval_kernel(const EvalArgs args, c
     constexpr int U = (MINB >= 2) ? kUnroll / 2 : kUnroll;
     extern __shared__ float4 s_fwd[];
     EvalArgs p = args;
-    if (LAYOUT == 0) {
+    if (LAYOUT == 0 || LAYOUT == 2) {
         float2* sP = reinterpret_cast<float2*>(s_fwd);
         float2* sS = sP + p.K;
         const int n_chain = p.hdr->n_chain_f;
         p.max_chain = p.hdr->max_chain_f;
         for (int i = threadIdx.x; i < p.K; i += blockDim.x) sP[i] = __ldg(p.recP + i);
-        if (p.s_staged)
+        if (LAYOUT == 2)
+            for (int i = threadIdx.x; i <= p.N; i += blockDim.x) sS[i] = __ldg(p.recS8 + i);
+        else if (p.s_staged)
             for (int i = threadIdx.x; i < 2 * (p.N + 1); i += blockDim.x) sS[i] = __ldg(p.recS + i);
         __syncthreads();
         // the chain walk out of line where the registers allow the call (one
         // CTA per SM); inline at two CTAs per SM (32 registers a thread)
+        constexpr bool S8 = LAYOUT == 2;
         if (n_chain == 0)
-            eval_body<IO, U>(p, Lerp8<false>{sP, sS, p}, x, y, m);
+            eval_body<IO, U>(p, Lerp8<false, false, S8>{sP, sS, p}, x, y, m);
         else
-            eval_body<IO, U>(p, Lerp8<true, MINB == 1>{sP, sS, p}, x, y, m);
+            eval_body<IO, U>(p, Lerp8<true, MINB == 1, S8>{sP, sS, p}, x, y, m);
     } else {
         const int n_chain = p.hdr->n_chain_b;
         p.max_chain = p.hdr->max_chain_b;
@@ -195,17 +210,20 @@ __global__ void __launch_bounds__(1024, MINB) eval_synth_kernel(const EvalArgs a
     EvalArgs p = args;
     const float w = __fsub_rn(p.b, p.a);
     float acc;
-    if (LAYOUT == 0) {
+    if (LAYOUT == 0 || LAYOUT == 2) {
         float2* sP = reinterpret_cast<float2*>(s_fwd);
         float2* sS = sP + p.K;
         const int n_chain = p.hdr->n_chain_f;
         p.max_chain = p.hdr->max_chain_f;
         for (int i = threadIdx.x; i < p.K; i += blockDim.x) sP[i] = __ldg(p.recP + i);
-        if (p.s_staged)
+        if (LAYOUT == 2)
+            for (int i = threadIdx.x; i <= p.N; i += blockDim.x) sS[i] = __ldg(p.recS8 + i);
+        else if (p.s_staged)
             for (int i = threadIdx.x; i < 2 * (p.N + 1); i += blockDim.x) sS[i] = __ldg(p.recS + i);
         __syncthreads();
-        acc = n_chain == 0 ? synth_sum(Lerp8<false>{sP, sS, p}, seed, p.a, w, m)
-                           : synth_sum(Lerp8<true>{sP, sS, p}, seed, p.a, w, m);
+        constexpr bool S8 = LAYOUT == 2;
+        acc = n_chain == 0 ? synth_sum(Lerp8<false, false, S8>{sP, sS, p}, seed, p.a, w, m)
+                           : synth_sum(Lerp8<true, false, S8>{sP, sS, p}, seed, p.a, w, m);
     } else {
         const int n_chain = p.hdr->n_chain_b;
         p.max_chain = p.hdr->max_chain_b;
@@ -405,6 +423,7 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
     EvalArgs p{};
     p.recP = t->recP;
     p.recS = t->recS;
+    p.recS8 = t->recS8;
     p.xk = t->xk;
     p.rec16 = t->rec16;
     p.hdr = t->hdr;
@@ -412,7 +431,14 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
     p.a = t->a;
     p.b = t->b;
     size_t smem;
-    if (layout == 0) {
+    if (layout == 2) {
+        p.K = (int)t->K;
+        p.s_staged = 1;
+        p.inv_w = t->inv_w;
+        p.off = t->off;
+        p.w = t->w;
+        smem = eval8c_smem_bytes(t);
+    } else if (layout == 0) {
         p.K = (int)t->K;
         p.s_staged = forward_side_staged(t->N) ? 1 : 0;
         p.inv_w = t->inv_w;
@@ -434,6 +460,8 @@ pwl_status launch_eval(pwl_table t, int layout, const IO* x, IO* y, int64_t m, c
     void (*kern)(const EvalArgs, const IO*, IO*, int64_t);
     if (layout == 0)
         kern = two ? eval_kernel<IO, 0, 2> : eval_kernel<IO, 0, 1>;
+    else if (layout == 2)
+        kern = two ? eval_kernel<IO, 2, 2> : eval_kernel<IO, 2, 1>;
     else
         kern = two ? eval_kernel<IO, 1, 2> : eval_kernel<IO, 1, 1>;
     int max_grid = 0;
@@ -453,6 +481,7 @@ pwl_status launch_synth(pwl_table t, int layout, uint32_t seed, int64_t m, doubl
     EvalArgs p{};
     p.recP = t->recP;
     p.recS = t->recS;
+    p.recS8 = t->recS8;
     p.xk = t->xk;
     p.rec16 = t->rec16;
     p.hdr = t->hdr;
@@ -460,7 +489,14 @@ pwl_status launch_synth(pwl_table t, int layout, uint32_t seed, int64_t m, doubl
     p.a = t->a;
     p.b = t->b;
     size_t smem;
-    if (layout == 0) {
+    if (layout == 2) {
+        p.K = (int)t->K;
+        p.s_staged = 1;
+        p.inv_w = t->inv_w;
+        p.off = t->off;
+        p.w = t->w;
+        smem = eval8c_smem_bytes(t);
+    } else if (layout == 0) {
         p.K = (int)t->K;
         p.s_staged = forward_side_staged(t->N) ? 1 : 0;
         p.inv_w = t->inv_w;
@@ -481,6 +517,8 @@ pwl_status launch_synth(pwl_table t, int layout, uint32_t seed, int64_t m, doubl
     void (*kern)(const EvalArgs, uint32_t, int64_t, double*);
     if (layout == 0)
         kern = two ? eval_synth_kernel<0, 2> : eval_synth_kernel<0, 1>;
+    else if (layout == 2)
+        kern = two ? eval_synth_kernel<2, 2> : eval_synth_kernel<2, 1>;
     else
         kern = two ? eval_synth_kernel<1, 2> : eval_synth_kernel<1, 1>;
     int max_grid = 0;
@@ -650,7 +688,7 @@ pwl_status pwl_eval_synthetic_variant(pwl_table t, int32_t mode, uint32_t seed, 
 {
     clear_error();
     if (!t) return fail(PWL_EINVAL, "table is NULL");
-    if (mode < 0 || mode > 5) return fail(PWL_EINVAL, "unknown mode %d", mode);
+    if (mode < 0 || mode > 6) return fail(PWL_EINVAL, "unknown mode %d", mode);
     if (m < 0 || m > ((int64_t)1 << 32)) return fail(PWL_EINVAL, "m must be in [0, 2^32]");
     if (!d_sum) return fail(PWL_EINVAL, "d_sum is NULL");
     int dev = -1;
@@ -658,6 +696,7 @@ pwl_status pwl_eval_synthetic_variant(pwl_table t, int32_t mode, uint32_t seed, 
     if (dev != t->device) return fail(PWL_EINVAL, "table lives on device %d, current device is %d", t->device, dev);
     if (m == 0) return PWL_OK;
     if (mode == 2 || mode == 3) return launch_synth(t, mode - 2, seed, m, d_sum, as_stream(stream));
+    if (mode == 6) return launch_synth(t, 2, seed, m, d_sum, as_stream(stream));
     StreamIO io{};
     io.m = m;
     io.seed = seed;
@@ -671,10 +710,11 @@ pwl_status pwl_eval_variant(pwl_table t, int32_t mode, const float* d_x, float* 
     clear_error();
     pwl_status st = check_common(t, d_x, d_y, m);
     if (st != PWL_OK) return st;
-    if (mode < 0 || mode > 5) return fail(PWL_EINVAL, "unknown mode %d", mode);
+    if (mode < 0 || mode > 6) return fail(PWL_EINVAL, "unknown mode %d", mode);
     if (m == 0) return PWL_OK;
     cudaStream_t s = as_stream(stream);
     if (mode == 2 || mode == 3) return launch_eval<float>(t, mode - 2, d_x, d_y, m, s);
+    if (mode == 6) return launch_eval<float>(t, 2, d_x, d_y, m, s);
     StreamIO io{};
     io.x = d_x;
     io.y = d_y;

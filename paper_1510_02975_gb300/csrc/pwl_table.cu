@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_b_kernel(
 __global__ void __launch_bounds__(kBuildThreads) table_index_f_kernel(
     int N, int K, float inv_w, float off, float w, float a, const float* __restrict__ xk,
     const float* __restrict__ vk, const float* __restrict__ slope, int* cj, float2* recP, float2* recS,
-    TableHeader* hdr)
+    float2* recS8, TableHeader* hdr)
 {
     __shared__ int s_maxchain;
     __shared__ int s_nchain;
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(kBuildThreads) table_index_f_kernel(
     for (int k = threadIdx.x; k <= N; k += blockDim.x) {
         recS[2 * k] = make_float2(vk[k], slope[k]);
         recS[2 * k + 1] = make_float2(vk[k], slope[k + 1]);
+        recS8[k] = make_float2(vk[k], slope[k + 1]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -258,7 +259,7 @@ pwl_status launch_build(pwl_table t, const double* d_knots, const double* d_valu
                                                      t->inv_h, t->cj, t->cpos, t->rec16, t->rec_b, t->hdr);
     PWL_CHECK_LAUNCH("table_index_b_kernel");
     table_index_f_kernel<<<1, kBuildThreads, 0, s>>>(N, (int)t->K, t->inv_w, t->off, t->w, t->a, t->xk, t->vk,
-                                                     t->slope, t->cj, t->recP, t->recS, t->hdr);
+                                                     t->slope, t->cj, t->recP, t->recS, t->recS8, t->hdr);
     PWL_CHECK_LAUNCH("table_index_f_kernel");
     return PWL_OK;
 }
@@ -324,10 +325,20 @@ void choose_cells(pwl_table t, float hmin, int64_t requested)
         // N = 4096, 6.2 TB/s at 190 KB against 5.35 TB/s at 206 KB and
         // 5.95 TB/s on the 16-byte index)
         constexpr size_t kOneCtaIndexBytes = 190 * 1024;
-        const int64_t cap1b = forward_cell_capacity(N, std::min<size_t>(di.smem_optin, kOneCtaIndexBytes));
-        if ((double)cap1b >= std::max<double>(need, 3.0 * (double)(N + 1))) {
+        const size_t one = std::min<size_t>(di.smem_optin, kOneCtaIndexBytes);
+        const int64_t cap1b = forward_cell_capacity(N, one);
+        // the same budget with one side record per knot instead of two
+        const size_t side8 = sizeof(float2) * (size_t)(N + 1);
+        const int64_t cap1c = side8 + 8 * 1024 <= one ? (int64_t)((one - side8) / sizeof(float2)) : 0;
+        const double min_cells = std::max<double>(need, 3.0 * (double)(N + 1));
+        if ((double)cap1b >= min_cells) {
             K = (int64_t)std::min<double>(want, (double)cap1b);
             t->layout = 0;
+        } else if ((double)cap1c >= min_cells) {
+            // (the Lorentzian N = 4096 table: 20.1 K chain-free cells in 190 KB,
+            // where two side records per knot left room for 15.5 K)
+            K = (int64_t)std::min<double>(want, (double)cap1c);
+            t->layout = 2;
         } else {
             K = (int64_t)std::min<double>(want, (double)cap1);
             t->layout = 1;
@@ -425,13 +436,15 @@ pwl_status pwl_table_build(const double* d_knots, const double* d_values, int64_
     const size_t bytes_b = align256(sizeof(float4) * ((size_t)t->Kb + n1));
     const size_t bytes_p = align256(sizeof(float2) * (size_t)t->K);
     const size_t bytes_s = align256(sizeof(float2) * 2 * n1);
-    if ((e = dev_malloc(&t->buf_rec, 2 * bytes_b + bytes_p + bytes_s)) != cudaSuccess)
+    const size_t bytes_s8 = align256(sizeof(float2) * n1);
+    if ((e = dev_malloc(&t->buf_rec, 2 * bytes_b + bytes_p + bytes_s + bytes_s8)) != cudaSuccess)
         return bail(cuda_fail(e, "cudaMalloc(records)"));
     char* r = static_cast<char*>(t->buf_rec);
     t->rec_b = reinterpret_cast<float4*>(r);
     t->rec16 = reinterpret_cast<float4*>(r + bytes_b);
     t->recP = reinterpret_cast<float2*>(r + 2 * bytes_b);
     t->recS = reinterpret_cast<float2*>(r + 2 * bytes_b + bytes_p);
+    t->recS8 = reinterpret_cast<float2*>(r + 2 * bytes_b + bytes_p + bytes_s);
     if ((st = launch_build(t, d_knots, d_values, true, s)) != PWL_OK) return bail(st);
     if ((e = cudaMemcpyAsync(&h, t->hdr, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -496,7 +509,8 @@ pwl_status pwl_table_get_info(pwl_table t, pwl_table_info* info)
     info->b = t->b;
     info->d_knots = t->xk;
     info->d_values = t->vstore;
-    info->eval_smem_bytes = t->layout == 0 ? eval8_smem_bytes(t) : eval16_smem_bytes(t);
+    info->eval_smem_bytes =
+        t->layout == 0 ? eval8_smem_bytes(t) : (t->layout == 2 ? eval8c_smem_bytes(t) : eval16_smem_bytes(t));
     info->layout = t->layout;
     info->backward_smem_bytes = backward_smem_bytes(t);
     return PWL_OK;

@@ -20,6 +20,13 @@ inline size_t eval8_smem_bytes(const pwl_table_s* t)
 {
     return sizeof(float2) * (size_t)t->K + (forward_side_staged(t->N) ? forward_side_bytes(t->N) : 0);
 }
+// 8-byte index with one side record per knot ({v_k, s_{k+1}}; a query left
+// of knot k takes s_k from the record of knot k - 1): K cell records plus
+// N+1 side records, always staged.
+inline size_t eval8c_smem_bytes(const pwl_table_s* t)
+{
+    return sizeof(float2) * ((size_t)t->K + (size_t)(t->N + 1));
+}
 // 16-byte index for the forward path: K_b cells and reserved chain records
 inline int64_t eval16_smem_records(const pwl_table_s* t)
 {

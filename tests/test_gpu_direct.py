@@ -235,7 +235,7 @@ def test_uniform_texture_variant_matches_oracle(pwl, workloads, N):
     t.close()
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5, 6])
 def test_synthetic_variant_checksums_match_oracle(pwl, workloads, mode):
     f = workloads.PAPER_FUNCTIONS["lorentzian"]
     t, xk, vk = _table(pwl, f, 1000, uniform=(mode == 5))

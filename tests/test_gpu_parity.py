@@ -138,10 +138,10 @@ def test_eval_any_cell_count(pwl, workloads, k_cells):
     x = workloads.uniform_queries(f, 100003, seed=7)
     x[:xk.size] = torch.tensor(xk, dtype=torch.float32, device="cuda")
     _check_eval(t(x), xk, vk, x)
-    for mode in (2, 3):
+    for mode in (2, 3, 6):
         y = t.variant(mode, x)
         _check_eval(y, xk, vk, x)
-        # exact at the knots in either index
+        # exact at the knots in every index
         assert np.array_equal(y[:xk.size].cpu().numpy().astype(np.float64), vk)
     t.close()
 
@@ -152,8 +152,31 @@ def test_eval_both_layouts_default_cells(pwl, workloads, name, N):
     f = workloads.PAPER_FUNCTIONS[name]
     t, xk, vk = _table_and_ref(pwl, f, N)
     x = workloads.normal_queries(f, (1 << 19) + 9, seed=4)
-    for mode in (2, 3):
+    for mode in (2, 3, 6):
         _check_eval(t.variant(mode, x), xk, vk, x)
+    t.close()
+
+
+def test_compact_side_records_for_the_largest_chain_free_index(pwl, workloads):
+    # the Lorentzian at N = 4096 needs ~20 K cells for a chain-free index:
+    # with one side record per knot it fits the one-CTA budget (layout 2);
+    # every lookup side of every knot matches the oracle, and layout 2 gives
+    # the same bits as the two-side-record index (mode 2) on the same cells
+    f = workloads.LORENTZIAN
+    t, xk, vk = _table_and_ref(pwl, f, 4096)
+    assert int(t.info["layout"]) == 2 and int(t.info["n_chain"]) == 0
+    assert t.info["eval_smem_bytes"] <= 190 * 1024
+    x = workloads.uniform_queries(f, (1 << 20) + 5, seed=3)
+    x[:xk.size] = torch.tensor(xk, dtype=torch.float32, device="cuda")
+    mids = 0.5 * (xk[1:] + xk[:-1])
+    x[xk.size:xk.size + mids.size] = torch.tensor(mids, dtype=torch.float32, device="cuda")
+    nb = np.nextafter(xk.astype(np.float32), np.float32(-np.inf))
+    x[xk.size + mids.size:2 * xk.size + mids.size] = torch.tensor(nb, device="cuda")
+    y = t(x)
+    _check_eval(y, xk, vk, x)
+    assert np.array_equal(y[:xk.size].cpu().numpy().astype(np.float64), vk)
+    assert torch.equal(y, t.variant(2, x))
+    assert torch.equal(y, t.variant(6, x))
     t.close()
 
 
@@ -371,7 +394,7 @@ def test_table_update_in_place(pwl, workloads):
     pwl.pwl_table_check(t.handle)
     xk, vk = round_knots(k2.cpu().numpy()), round_values(v2.cpu().numpy(), "fp32")
     _check_eval(t(x), xk, vk, x)
-    for mode in (2, 3):
+    for mode in (2, 3, 6):
         _check_eval(t.variant(mode, x), xk, vk, x)
     # the texture filter follows the new values (8-bit weight bound)
     xs = x.cpu().numpy().astype(np.float64)
