@@ -916,10 +916,11 @@ def run_variants(args):
                     row["layout"] = int(t.info["layout"])
                     for label, fn in (("main", lambda: pwl.pwl_eval(t.handle, x, y)),
                                       ("cells8", lambda: pwl.pwl_eval_variant(t.handle, 2, x, y)),
+                                      ("cells8_one_side_record", lambda: pwl.pwl_eval_variant(t.handle, 6, x, y)),
                                       ("cells16", lambda: pwl.pwl_eval_variant(t.handle, 3, x, y)),
                                       ("search", lambda: pwl.pwl_eval_variant(t.handle, 0, x, y)),
                                       ("texture", lambda: pwl.pwl_eval_variant(t.handle, 1, x, y))):
-                        if dt != "fp32" and label in ("search", "cells8", "cells16"):
+                        if dt != "fp32" and label in ("search", "cells8", "cells8_one_side_record", "cells16"):
                             continue
                         sec = time_launches(fn)
                         row[label + "_gbs"] = round(BYTES_FWD * m / sec / 1e9, 1)
