@@ -142,6 +142,20 @@ __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ Gaus
 // The rows are assembled on the fly (M_{i,i-1} = h_i/6, M_ii = (h_i +
 // h_{i+1})/3, M_{i,i+1} = h_{i+1}/6, b_i = R_i + L_{i+1}).  About 20 FP64
 // operations per row, one division; no barrier beyond the warp.
+// 1/d for a positive normal FP64 d by Newton's method for the reciprocal,
+// r <- r + r (1 - d r), from the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64); each step doubles the correct bits, two reach FP64
+// rounding.  Five FP64 operations against about twice that for a division.
+__device__ __forceinline__ double recip_newton(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 __global__ void __launch_bounds__(64) gram_spike_kernel(ProjectPlan p, const int* __restrict__ order)
 {
     const int lane = threadIdx.x & 31;
@@ -161,14 +175,17 @@ __global__ void __launch_bounds__(64) gram_spike_kernel(ProjectPlan p, const int
         if (lane < P) {
             // forward elimination of the block, three right-hand sides
             double cprev = 0.0, yprev = 0.0, vprev = 0.0, wlast = 0.0;
+            // the interval left of row i carries over from the previous row
+            double xi = x[r0];
+            double hl = r0 > 0 ? xi - x[r0 - 1] : 0.0;
 #pragma unroll 4
             for (int i = r0; i < r1; ++i) {
-                const double hl = i > 0 ? x[i] - x[i - 1] : 0.0;
-                const double hr = i < N ? x[i + 1] - x[i] : 0.0;
+                const double xn = i < N ? x[i + 1] : xi;
+                const double hr = xn - xi;
                 const double rhs = (i > 0 ? lr[i - 1].y : 0.0) + (i < N ? lr[i].x : 0.0);
                 const double lower = i > r0 ? hl * kSixth : 0.0;  // coupling inside the block
                 const double upper = hr * kSixth;
-                const double r = 1.0 / ((hl + hr) * kThird - lower * cprev);
+                const double r = recip_newton((hl + hr) * kThird - lower * cprev);
                 const double yv = (rhs - lower * yprev) * r;
                 const double vv = ((i == r0 ? hl * kSixth : 0.0) - lower * vprev) * r;
                 cprev = i + 1 < r1 ? upper * r : 0.0;
@@ -178,6 +195,8 @@ __global__ void __launch_bounds__(64) gram_spike_kernel(ProjectPlan p, const int
                 sc[4 * i + 2] = vv;
                 yprev = yv;
                 vprev = vv;
+                hl = hr;
+                xi = xn;
             }
             // back substitution: y_j, v_j, w_j (w' is zero above the last row)
             double yn = 0.0, vn = 0.0, wn = 0.0;
