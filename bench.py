@@ -234,6 +234,7 @@ class Workload:
             self.x[(fi, "normal")] = W.normal_queries(f, self.m, seed=2)
         self.y = torch.empty(self.m, dtype=torch.float32, device="cuda")
         self.items = []  # (fi, N, knots, vi, vp, ws_d, ws_p, table_i, table_p)
+        self.wsp2 = []   # a second projection workspace per item (the two forms run side by side)
         lib = pwl._capi.load()
         for fi, f in enumerate(self.funcs):
             for N in NS:
@@ -245,37 +246,47 @@ class Workload:
                 ti = pwl.Table(kn, vi)
                 tp = pwl.Table(kn, vp)
                 self.items.append((fi, N, kn, vi, vp, wsd, wsp, ti, tp))
+                self.wsp2.append(torch.empty_like(wsp))
         torch.cuda.synchronize()
         self.capture_design()
         self.evals_per_step = len(self.items) * len(FORMS) * 2 * self.m
 
-    def _design_item(self, item):
-        pwl = self.pwl
-        fi, N, kn, vi, vp, wsd, wsp, ti, tp = item
+    def _design_item(self, k, st, side):
+        """Item k on stream st: the design, then the interpolant's values and
+        its table rebuild on st and, side by side on `side`, the projection's
+        values and its table rebuild (both need only the knots)."""
+        torch, pwl = self.torch, self.pwl
+        fi, N, kn, vi, vp, wsd, wsp, ti, tp = self.items[k]
         f = self.funcs[fi]
-        pwl.pwl_design(f, N, 0, "fp64", knots=kn, workspace=wsd)
-        pwl.pwl_project(f, kn, "interp", values=vi, workspace=wsp)
-        pwl.pwl_project(f, kn, "project", values=vp, workspace=wsp)
-        ti.update(kn, vi)
-        tp.update(kn, vp)
+        with torch.cuda.stream(st):
+            pwl.pwl_design(f, N, 0, "fp64", knots=kn, workspace=wsd)
+        side.wait_stream(st)
+        with torch.cuda.stream(st):
+            pwl.pwl_project(f, kn, "interp", values=vi, workspace=wsp)
+            ti.update(kn, vi)
+        with torch.cuda.stream(side):
+            pwl.pwl_project(f, kn, "project", values=vp, workspace=self.wsp2[k])
+            tp.update(kn, vp)
+        st.wait_stream(side)
 
     def capture_design(self):
         """Design, both projections and both table rebuilds of every
-        (function, N) captured once into a CUDA graph, one parallel branch per
-        (function, N); a step replays it."""
+        (function, N) captured once into a CUDA graph: a branch per
+        (function, N), forked after the design into one branch per form; a
+        step replays it."""
         torch = self.torch
-        for item in self.items:  # eager pass: sets kernel attributes outside capture
-            self._design_item(item)
+        cur = torch.cuda.current_stream()
+        for k in range(len(self.items)):  # eager pass: sets kernel attributes outside capture
+            self._design_item(k, cur, cur)
         torch.cuda.synchronize()
-        self.streams = [torch.cuda.Stream() for _ in self.items]
+        self.streams = [(torch.cuda.Stream(), torch.cuda.Stream()) for _ in self.items]
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
             main = torch.cuda.current_stream()
-            for st, item in zip(self.streams, self.items):
+            for k, (st, side) in enumerate(self.streams):
                 st.wait_stream(main)
-                with torch.cuda.stream(st):
-                    self._design_item(item)
-            for st in self.streams:
+                self._design_item(k, st, side)
+            for st, _ in self.streams:
                 main.wait_stream(st)
         torch.cuda.synchronize()
 
