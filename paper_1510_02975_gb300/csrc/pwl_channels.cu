@@ -345,12 +345,14 @@ __device__ __forceinline__ void chan_fwd8_rows(const ChanArgs& p, int64_t c0, in
     const ChanConstF cc(tp, ch);
     int64_t r = r0 + threadIdx.x / kChF;
     const int64_t pass = (int64_t)kRowsPerPassF * p.C;  // elements between a thread's consecutive rows
+    // x is read at the L2 only (ld.global.cg): 2% faster than through L1,
+    // whose lines the row segments of other CTAs do not share anyway
     const IO* px = x + r * p.C + c;
     IO* py = y + r * p.C + c;
     for (; r + (int64_t)(kChUnrollF - 1) * kRowsPerPassF < r1; r += (int64_t)kChUnrollF * kRowsPerPassF) {
         float v[kChUnrollF];
 #pragma unroll
-        for (int u = 0; u < kChUnrollF; ++u) v[u] = to_f32<IO>(px[u * pass]);
+        for (int u = 0; u < kChUnrollF; ++u) v[u] = to_f32<IO>(__ldcg(px + u * pass));
 #pragma unroll
         for (int u = 0; u < kChUnrollF; ++u) v[u] = chan_fwd8<CHAINS>(v[u], ch, R, xs, vs, sp, cc, p.N, p.K);
 #pragma unroll
@@ -366,7 +368,7 @@ __device__ __forceinline__ void chan_fwd8_rows(const ChanArgs& p, int64_t c0, in
         float v[kChTailF];
 #pragma unroll
         for (int u = 0; u < kChTailF; ++u)
-            if (u < rem) v[u] = to_f32<IO>(px[u * pass]);
+            if (u < rem) v[u] = to_f32<IO>(__ldcg(px + u * pass));
 #pragma unroll
         for (int u = 0; u < kChTailF; ++u)
             if (u < rem) st_cs(py + u * pass, from_f32<IO>(chan_fwd8<CHAINS>(v[u], ch, R, xs, vs, sp, cc, p.N, p.K)));
