@@ -318,7 +318,6 @@ __global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan
     __shared__ double s_G[kDesignThreads];  // delta * s_S: G at each thread's first cell
     __shared__ double s_warp[kDesignThreads / 32 + 1];
     __shared__ int s_last;
-    __shared__ int64_t s_range[2];
     const int t = threadIdx.x;
     for (int o = blockIdx.x; o < p.F; o += gridDim.x) {
         const int f = p.order[o];
@@ -375,17 +374,17 @@ __global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan
             __syncthreads();
             continue;
         }
+        // the first target of every chunk, all chunks at once (the chunk sums
+        // are spent: their area takes the indices)
+        int64_t* ifirst = reinterpret_cast<int64_t*>(csum);
+        for (int64_t c = t; c < nch; c += kDesignThreads) ifirst[c] = first_target_at_or_above(delta * cbase[c], GM, N);
+        __syncthreads();
 
         // pass B
         int64_t lastpos = -1;  // last cell of positive density before the current chunk
         for (int64_t ch = 0; ch < nch; ++ch) {
             const int64_t c0 = ch * kChunk;
-            if (t == 0) {
-                s_range[0] = first_target_at_or_above(delta * cbase[ch], GM, N);
-                s_range[1] = ch + 1 < nch ? first_target_at_or_above(delta * cbase[ch + 1], GM, N) : N;
-            }
-            __syncthreads();
-            const int64_t i0 = s_range[0], i1 = s_range[1];
+            const int64_t i0 = ifirst[ch], i1 = ch + 1 < nch ? ifirst[ch + 1] : N;
             if (i0 < i1) {
                 const int cnt = (int)min((int64_t)kChunk, M - c0);
                 const float t0f = (float)(a + (double)c0 * delta);
@@ -454,7 +453,7 @@ __global__ void __launch_bounds__(kDesignThreads) design_fused_kernel(DesignPlan
             }
             const int cl = clast[ch];
             if (cl >= 0) lastpos = c0 + cl;
-            __syncthreads();  // s_d, s_S and s_range are rewritten for the next chunk
+            __syncthreads();  // s_d and s_S are rewritten for the next chunk
         }
     }
 }
@@ -582,7 +581,6 @@ __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(De
     __shared__ int s_last2[2];
     __shared__ double s_warp[kDesignThreads / 32 + 1];
     __shared__ int s_last;
-    __shared__ int64_t s_range[2];
     const int t = threadIdx.x;
     float* __restrict__ dbuf_all = reinterpret_cast<float*>(p.d);
     if (t < 2) s_last2[t] = -1;
@@ -646,17 +644,17 @@ __global__ void __launch_bounds__(kDesignThreads, 4) design_fused_fp32_kernel(De
             continue;
         }
         const double cunit = carry / (double)N;  // tau_i / delta = i * cunit
+        // the first target of every chunk, all chunks at once (the chunk sums
+        // are spent: their area takes the indices)
+        int64_t* ifirst = reinterpret_cast<int64_t*>(csum);
+        for (int64_t c = t; c < nch; c += kDesignThreads) ifirst[c] = first_target_at_or_above_units(cbase[c], cunit, N);
+        __syncthreads();
 
         // pass B
         int64_t lastpos = -1;
         for (int64_t ch = 0; ch < nch; ++ch) {
             const int64_t c0 = ch * kChunk;
-            if (t == 0) {
-                s_range[0] = first_target_at_or_above_units(cbase[ch], cunit, N);
-                s_range[1] = ch + 1 < nch ? first_target_at_or_above_units(cbase[ch + 1], cunit, N) : N;
-            }
-            __syncthreads();
-            const int64_t i0 = s_range[0], i1 = s_range[1];
+            const int64_t i0 = ifirst[ch], i1 = ch + 1 < nch ? ifirst[ch + 1] : N;
             if (i0 < i1) {
                 const int cnt = (int)min((int64_t)kChunk, M - c0);
                 FF part{0.0f, 0.0f};

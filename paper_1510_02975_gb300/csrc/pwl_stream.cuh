@@ -76,8 +76,8 @@ struct Vec<__half> {
 };
 
 // streaming (evict-first) 16-byte global accesses
-__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
-__device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcg(p); }
 __device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
 __device__ __forceinline__ void st_stream(uint4* p, uint4 v) { __stcs(p, v); }
 
