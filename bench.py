@@ -196,6 +196,19 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+EVAL_SOURCES = ("pwl_eval.cu", "pwl_stream.cuh", "pwl_common.cuh", "pwl_table.cuh")
+
+
+def eval_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the evaluation kernel's sources
+    (the .cu and the headers its kernel code comes from), concatenated."""
+    h = hashlib.sha256()
+    for name in EVAL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1510_02975_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic():
     """Per-launch DRAM bytes of the evaluation kernel from the last ncu
     capture, or None if the kernel source changed since."""
@@ -206,9 +219,7 @@ def recorded_traffic():
         if "=" in ln and not ln.startswith("#"):
             k, v = ln.split("=", 1)
             vals[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_1510_02975_gb300", "csrc", "pwl_eval.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if vals.get("source_sha256_16") != h:
+    if vals.get("source_sha256_16") != eval_source_hash():
         return None
     try:
         return float(vals["bytes_per_launch_full_size"])

@@ -14,6 +14,12 @@ Tolerances (from the arithmetic):
     eps N (G(x_i) / G_M) h_i, so each knot is held within
     max(1e-3, 1e-6 N) of the shorter of its two intervals (eps up to ~1e-6:
     the FP32 f'' of J0 near its zeros).
+  FP32 integrand mode of the vertex values: f is evaluated in FP32 at
+    FP32-rounded points, so each f(t) carries |t f'(t)| 2^-24 from the
+    argument plus the FP32 function's own error (below 2^-18 max|f| for the
+    library J0); v_i = f(x_i) takes that once, and P_T's hat sums average it
+    and the Gram solve (its diagonal scaling has off-diagonal row sums 1/2)
+    at most doubles it: |v - v_ref| <= 2.5 env (fp32_integrand_envelope).
 """
 import numpy as np
 
@@ -21,6 +27,15 @@ EVAL_REL = 5e-7
 DESIGN_REL = 1e-12
 VALUES_REL = 1e-12
 GRAD_REL = 1e-5
+
+
+def fp32_integrand_envelope(desc, samples: int = 20001) -> float:
+    """max|f| 2^-18 + max|t f'(t)| 2^-24 over [a, b] (f from the oracle,
+    f' by central differences on `samples` points)."""
+    import oracle
+    t = np.linspace(desc["a"], desc["b"], samples)
+    ft = oracle.f_many(desc, t)
+    return float(np.abs(ft).max() * 2.0 ** -18 + np.abs(t * np.gradient(ft, t)).max() * 2.0 ** -24)
 
 
 def fp32_design_bound(ref_knots) -> np.ndarray:

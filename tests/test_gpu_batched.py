@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from pwl_testutil import DESIGN_REL, EVAL_REL, VALUES_REL, fp32_design_bound, round_knots
+from pwl_testutil import DESIGN_REL, EVAL_REL, VALUES_REL, fp32_design_bound, fp32_integrand_envelope, round_knots
 
 pytestmark = pytest.mark.gpu
 
@@ -92,6 +92,42 @@ def test_batch_design_values_eval_match_oracle(pwl, workloads, form, F):
     b.plan(qo)
     y = b.eval(xd).cpu().numpy()
     _check_batch_eval(b, funcs, qo, x, y)
+    b.close()
+
+
+@pytest.mark.parametrize("F", [40, 70])
+def test_batch_fp32_projection_within_integrand_rounding(pwl, workloads, F):
+    # FP32 integrand mode with both solvers (F = 40: cyclic reduction, one
+    # CTA per function; F = 70: partitioned Thomas, one warp per function)
+    # against the oracle's P_T values on the same knots
+    funcs, n_int, _, _ = _batch_inputs(workloads, F, seed=21)
+    b = pwl.Batch(funcs, n_int, m_per_interval=16)
+    b.design()
+    b.project("project", 8, "fp32")
+    knots = b.knots().cpu().numpy()
+    vals = b.values().cpu().numpy()
+    off = b.offsets()
+    for i, f in enumerate(funcs):
+        kn = knots[off[i]:off[i + 1]]
+        vref = oracle.values(f, kn, "project")
+        assert np.abs(vals[off[i]:off[i + 1]] - vref).max() <= 2.5 * fp32_integrand_envelope(f), i
+    b.close()
+
+
+@pytest.mark.parametrize("F", [40, 70])
+def test_batch_fp32_projection_of_a_constant_is_exact(pwl, F):
+    # a constant is exact in FP32 and in the CPWL space (the hats sum to one),
+    # so P_T gives it back at every vertex: what remains is the error of the
+    # float-float hat sums and of the FP64 solve, far below FP32 rounding
+    c = 0.7503662109375  # 2^-1 + ... : exact in FP32
+    funcs = [{"kind": "poly", "a": -3.0 + 0.01 * k, "b": 2.0 + 0.37 * k, "p": [c, 0, 0, 0, 0, 0, 0, 0]}
+             for k in range(F)]
+    n_int = [1 + (37 * k) % 900 for k in range(F)]
+    b = pwl.Batch(funcs, n_int, m_per_interval=4)
+    b.design()
+    b.project("project", 8, "fp32")
+    vals = b.values().cpu().numpy()
+    assert np.abs(vals - c).max() <= 1e-12 * c
     b.close()
 
 

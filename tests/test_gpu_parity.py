@@ -5,7 +5,8 @@ import numpy as np
 import pytest
 
 import oracle
-from pwl_testutil import DESIGN_REL, EVAL_REL, GRAD_REL, VALUES_REL, fp32_design_bound, round_knots, round_values
+from pwl_testutil import (DESIGN_REL, EVAL_REL, GRAD_REL, VALUES_REL, fp32_design_bound, fp32_integrand_envelope,
+                          round_knots, round_values)
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +77,24 @@ def test_values_match_oracle(pwl, workloads, name, form, N):
     got = pwl.pwl_project(f, knots, form).cpu().numpy()
     ref = oracle.values(f, kn, form)
     assert np.abs(got - ref).max() <= VALUES_REL * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", FUNCS)
+@pytest.mark.parametrize("form", ["interp", "project"])
+@pytest.mark.parametrize("N", [63, 1024])
+def test_values_fp32_integrand_within_its_rounding(pwl, workloads, name, form, N):
+    # FP32 integrand mode against the FP64 oracle on the same knots, within
+    # the envelope of FP32 evaluation (pwl_testutil.fp32_integrand_envelope)
+    f = workloads.PAPER_FUNCTIONS[name]
+    knots = pwl.pwl_design(f, N)
+    kn = knots.cpu().numpy()
+    got = pwl.pwl_project(f, knots, form, 8, "fp32").cpu().numpy()
+    ref = oracle.values(f, kn, form)
+    env = fp32_integrand_envelope(f)
+    err = np.abs(got - ref).max()
+    assert err <= 2.5 * env, (err, env)
+    # and not FP64-exact by accident: the mode's rounding is visible
+    assert err > 0.0
 
 
 def test_projection_large_n_global_solver(pwl, workloads):
