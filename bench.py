@@ -201,11 +201,16 @@ EVAL_SOURCES = ("pwl_eval.cu", "pwl_stream.cuh", "pwl_common.cuh", "pwl_table.cu
 
 def eval_source_hash() -> str:
     """First 16 hex digits of the SHA-256 of the evaluation kernel's sources
-    (the .cu and the headers its kernel code comes from), concatenated."""
+    (the .cu and the headers its kernel code comes from), concatenated, with
+    comments and whitespace removed: an edit of a comment keeps the record."""
+    import re
     h = hashlib.sha256()
     for name in EVAL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1510_02975_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1510_02975_gb300", "csrc", name), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(re.sub(r"\s+", "", text).encode())
     return h.hexdigest()[:16]
 
 
