@@ -345,9 +345,14 @@ pwl_status pwl_direct_synthetic(const pwl_func* f, int32_t method, uint32_t seed
  * with dy/dv_{i-1} = 1 - delta, dy/dv_i = delta, dy/dx_{i-1} = -s (1 - delta),
  * dy/dx_i = -s delta; a clamped query adds gy to g_values[0] or [N] only.
  * g_values / g_knots are accumulated into (the caller zeroes them).  Each
- * CTA accumulates with FP32 shared-memory atomics; the CTA partial sums are
- * then reduced in a fixed order in FP64, so run-to-run differences stay at
- * the FP32 rounding level of the in-CTA sums.  gx may alias gy.
+ * CTA accumulates the per-interval sums in 32-bit fixed point with integer
+ * shared-memory atomics: its unit is 2^-F with 2^F ~ 2^23 / (geometric mean
+ * of the |gy| among its first queries), each term is rounded to the unit
+ * once (absolute error <= 2^-(F+1)), integer wraps are counted exactly, and
+ * terms of 2^31 units or more (or inf, NaN) are summed in FP32 instead.  The
+ * CTA partial sums are then reduced in a fixed order in FP64; run-to-run
+ * differences come only from the order of the FP32-summed terms (none for
+ * gradients of moderate range).  gx may alias gy.
  * Workspace: pwl_eval_backward_workspace_size(t) bytes.                    */
 size_t pwl_eval_backward_workspace_size(pwl_table t);
 pwl_status pwl_eval_backward(pwl_table t, const float* d_x, const float* d_gy, float* d_gx,

@@ -11,16 +11,28 @@
 //
 // Pass 1 (persistent grid): every CTA stages the backward records (in up to
 // 8 bank-private copies) and the reciprocal lengths, streams (x, gy) -> gx
-// with 16-byte vectors, and accumulates A, B in shared memory: per-lane FP32
+// with 16-byte vectors, and accumulates A, B in shared memory: per-lane
 // atomics into up to 32 accumulator copies for random queries, a warp-level
 // sum for vectors that lie in one or two intervals (sorted or clustered
 // queries), and registers for a warp's hot interval (a point mass) and for
 // the queries at or beyond the ends of [a, b].  It then writes its partial
 // sums to the workspace (one row per CTA).
+// The shared-memory sums are 32-bit fixed point (FP32 shared-memory atomic
+// adds are a compare-and-swap loop in software; 32-bit integer adds are a
+// single native operation, ~4x the throughput with random bins).  Each CTA
+// picks its unit 2^-F from the geometric mean of the |gy| in its first
+// vectors, so that a typical term is ~2^22 units; a term t = rint(c 2^F)
+// then carries an absolute error of at most half a unit.  The int32 adds
+// wrap modulo 2^32, and the lane whose add wraps (seen from the old value
+// the atomic returns: exactly one lane per wrap) adds +-2^32 units to the
+// CTA's row in global memory, so every sum is exact in integer arithmetic
+// whatever the order of the adds.  Terms of 2^31 units or more (and inf,
+// NaN) are added to the row as FP32 instead (global FP32 reductions are
+// native).
 // Pass 2: 32 knots per CTA, the CTA rows split over 16 thread groups, sums
-// the rows in a fixed order (FP64) and forms g_v and g_x (the order of the
-// in-CTA atomics still varies from run to run, so the sums are reproducible
-// to FP32 rounding, not bit for bit).
+// the rows in a fixed order (FP64) and forms g_v and g_x (the in-CTA integer
+// sums do not depend on the order of the adds; the few FP32 terms of a row
+// do, so results are reproducible to their rounding).
 #include <math.h>
 
 #include <algorithm>
@@ -34,7 +46,8 @@ namespace {
 
 constexpr int kBwdUnroll = 2;
 
-// Accumulator layout per CTA row (FP32, 2 (N + 2) entries):
+// Accumulator layout per CTA row (2 (N + 2) entries; int32 fixed point in
+// shared memory, FP32 in the row):
 //   A[0]      gy of queries clamped on the left  -> g_v[0]
 //   A[1..N]   sum gy (1 - delta) on interval i
 //   A[N+1]    gy of queries clamped on the right -> g_v[N]
@@ -50,7 +63,28 @@ struct BwdArgs {
     float a, b, inv_w, off;
     float s_first, s_last;  // slopes of intervals 1 and N (set by the kernel)
     int64_t nvec;       // float4 vectors (x, gy and gx all 16-byte aligned), else 0
+    // set by the kernel: the CTA's fixed-point unit 2^-F (scale = 2^F), the
+    // value of one int32 wrap (2^(32-F)) and the CTA's row (A columns at
+    // rowA, B columns at rowB = rowA + N + 2)
+    float scale, wrap;
+    float* rowA;
+    float* rowB;
 };
+
+// Fixed-point add of the scaled term vs = v 2^F into a shared accumulator:
+// one native atomic, a wrap reported to the row as +-2^(32-F); terms outside
+// the int32 range (and inf, NaN) go to the row as FP32.
+__device__ __forceinline__ void fix_add(int* acc, float* grow, float vs, float v, float wrap)
+{
+    if (fabsf(vs) < 0x1p31f) {
+        const int t = __float2int_rn(vs);
+        const int old = atomicAdd(acc, t);
+        const int nw = (int)((unsigned)old + (unsigned)t);
+        if (((old ^ nw) & ~(old ^ t)) < 0) atomicAdd(grow, t < 0 ? -wrap : wrap);
+    } else {
+        atomicAdd(grow, v);
+    }
+}
 
 // Queries at or beyond the ends of [a, b] all feed the same four sums; a
 // skewed input (a query set clipped to the domain) can send half of them
@@ -110,26 +144,37 @@ __device__ __forceinline__ float bwd_query(float x, float g, const float4* __res
     return gx;
 }
 
-// A query's two sums into its lane's accumulator copy (one predicated pair
-// of shared-memory atomics; a divergent version issued them once per path)
-__device__ __forceinline__ void bwd_scatter(float* accA, float* accB, int bin, float ca, float cb, int lanes,
+// A query's two sums into its lane's accumulator copy: both terms share the
+// range check (|ca| + |cb| = |gy|), the rare out-of-range query adds both to
+// the row as FP32
+__device__ __forceinline__ void bwd_scatter(int* accA, int* accB, int bin, float ca, float cb, const BwdArgs& p,
                                             int copy)
 {
     if (bin >= 0) {
-        atomicAdd(accA + bin * lanes + copy, ca);
-        atomicAdd(accB + bin * lanes + copy, cb);
+        const float sa = ca * p.scale, sb = cb * p.scale;
+        if (fabsf(sa) + fabsf(sb) < 0x1p31f) {
+            const int ta = __float2int_rn(sa), tb = __float2int_rn(sb);
+            const int oa = atomicAdd(accA + bin * p.lanes + copy, ta);
+            const int ob = atomicAdd(accB + bin * p.lanes + copy, tb);
+            const int na = (int)((unsigned)oa + (unsigned)ta), nb = (int)((unsigned)ob + (unsigned)tb);
+            if (((oa ^ na) & ~(oa ^ ta)) < 0) atomicAdd(p.rowA + bin, ta < 0 ? -p.wrap : p.wrap);
+            if (((ob ^ nb) & ~(ob ^ tb)) < 0) atomicAdd(p.rowB + bin, tb < 0 ? -p.wrap : p.wrap);
+        } else {
+            atomicAdd(p.rowA + bin, ca);
+            atomicAdd(p.rowB + bin, cb);
+        }
     }
 }
 
 template <bool CHAINS>
 __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restrict__ srec,
-                                         const float* __restrict__ s_ih, float* accA, float* accB,
+                                         const float* __restrict__ s_ih, int* accA, int* accB,
                                          EndSums& e, const BwdArgs& p, int copy)
 {
     int bin;
     float ca, cb;
     const float gx = bwd_query<CHAINS>(x, g, srec, s_ih, e, p, bin, ca, cb);
-    bwd_scatter(accA, accB, bin, ca, cb, p.lanes, copy);
+    bwd_scatter(accA, accB, bin, ca, cb, p, copy);
     return gx;
 }
 
@@ -161,7 +206,7 @@ constexpr int kHotLanes = 8;
 
 // The hot interval's sums into shared memory (warp-uniform call: every lane
 // of the warp runs it)
-__device__ __forceinline__ void flush_hot(float* accA, float* accB, HotBin& h, int lanes, int lane)
+__device__ __forceinline__ void flush_hot(int* accA, int* accB, HotBin& h, const BwdArgs& p, int lane)
 {
     if (h.bin < 0) return;
     for (int o = 16; o > 0; o >>= 1) {
@@ -169,21 +214,21 @@ __device__ __forceinline__ void flush_hot(float* accA, float* accB, HotBin& h, i
         h.b += __shfl_xor_sync(0xffffffffu, h.b, o);
     }
     if (lane == 0) {
-        atomicAdd(accA + h.bin * lanes, h.a);
-        atomicAdd(accB + h.bin * lanes, h.b);
+        fix_add(accA + h.bin * p.lanes, p.rowA + h.bin, h.a * p.scale, h.a, p.wrap);
+        fix_add(accB + h.bin * p.lanes, p.rowB + h.bin, h.b * p.scale, h.b, p.wrap);
     }
     h.a = 0.0f;
     h.b = 0.0f;
 }
 
 // A query's sums: into the hot interval's registers, or the lane's copy
-__device__ __forceinline__ void bwd_scatter_hot(float* accA, float* accB, int bin, float ca, float cb, int lanes,
-                                                int copy, HotBin& h)
+__device__ __forceinline__ void bwd_scatter_hot(int* accA, int* accB, int bin, float ca, float cb,
+                                                const BwdArgs& p, int copy, HotBin& h)
 {
     const bool hit = bin == h.bin;
     h.a += hit ? ca : 0.0f;
     h.b += hit ? cb : 0.0f;
-    bwd_scatter(accA, accB, hit ? -1 : bin, ca, cb, lanes, copy);
+    bwd_scatter(accA, accB, hit ? -1 : bin, ca, cb, p, copy);
 }
 
 // Four consecutive queries per lane, 128 per warp, all 32 lanes active.
@@ -201,7 +246,7 @@ __device__ __forceinline__ void bwd_scatter_hot(float* accA, float* accB, int bi
 // back to per-lane atomics and switches back.
 template <bool CHAINS>
 __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float4* __restrict__ srec,
-                                               const float* __restrict__ s_ih, float* accA, float* accB,
+                                               const float* __restrict__ s_ih, int* accA, int* accB,
                                                EndSums& e, const BwdArgs& p, int copy, int lane, bool detect,
                                                bool& agg, HotBin& hot)
 {
@@ -211,29 +256,29 @@ __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float
         float ca, cb;
         if (hot.bin < 0) {
             o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
-            bwd_scatter(accA, accB, bin[0], ca, cb, p.lanes, copy);
+            bwd_scatter(accA, accB, bin[0], ca, cb, p, copy);
             o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
-            bwd_scatter(accA, accB, bin[1], ca, cb, p.lanes, copy);
+            bwd_scatter(accA, accB, bin[1], ca, cb, p, copy);
             o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
-            bwd_scatter(accA, accB, bin[2], ca, cb, p.lanes, copy);
+            bwd_scatter(accA, accB, bin[2], ca, cb, p, copy);
             o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
-            bwd_scatter(accA, accB, bin[3], ca, cb, p.lanes, copy);
+            bwd_scatter(accA, accB, bin[3], ca, cb, p, copy);
         } else {
             o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
-            bwd_scatter_hot(accA, accB, bin[0], ca, cb, p.lanes, copy, hot);
+            bwd_scatter_hot(accA, accB, bin[0], ca, cb, p, copy, hot);
             o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
-            bwd_scatter_hot(accA, accB, bin[1], ca, cb, p.lanes, copy, hot);
+            bwd_scatter_hot(accA, accB, bin[1], ca, cb, p, copy, hot);
             o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
-            bwd_scatter_hot(accA, accB, bin[2], ca, cb, p.lanes, copy, hot);
+            bwd_scatter_hot(accA, accB, bin[2], ca, cb, p, copy, hot);
             o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
-            bwd_scatter_hot(accA, accB, bin[3], ca, cb, p.lanes, copy, hot);
+            bwd_scatter_hot(accA, accB, bin[3], ca, cb, p, copy, hot);
         }
         if (detect) {
             const int b0 = __shfl_sync(0xffffffffu, bin[0], 0);
             const unsigned same = __ballot_sync(0xffffffffu, bin[0] >= 0 && bin[0] == b0);
             agg = same == 0xffffffffu;
             if (!agg && b0 != hot.bin && __popc(same) >= kHotLanes) {
-                flush_hot(accA, accB, hot, p.lanes, lane);
+                flush_hot(accA, accB, hot, p, lane);
                 hot.bin = b0;
             }
         }
@@ -262,23 +307,23 @@ __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float
             bLs += __shfl_xor_sync(0xffffffffu, bLs, o2);
         }
         if (lane == 0) {
-            atomicAdd(accA + bF * p.lanes, aF);
-            atomicAdd(accB + bF * p.lanes, bFs);
+            fix_add(accA + bF * p.lanes, p.rowA + bF, aF * p.scale, aF, p.wrap);
+            fix_add(accB + bF * p.lanes, p.rowB + bF, bFs * p.scale, bFs, p.wrap);
         } else if (lane == 1 && bL != bF) {
             const int c1 = 1 & (p.lanes - 1);
-            atomicAdd(accA + bL * p.lanes + c1, aL);
-            atomicAdd(accB + bL * p.lanes + c1, bLs);
+            fix_add(accA + bL * p.lanes + c1, p.rowA + bL, aL * p.scale, aL, p.wrap);
+            fix_add(accB + bL * p.lanes + c1, p.rowB + bL, bLs * p.scale, bLs, p.wrap);
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) bwd_scatter(accA, accB, bin[k], ca[k], cb[k], p.lanes, copy);
+        for (int k = 0; k < 4; ++k) bwd_scatter(accA, accB, bin[k], ca[k], cb[k], p, copy);
     }
     return o;
 }
 
 template <bool CHAINS>
 __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __restrict__ srec,
-                                              const float* __restrict__ s_ih, float* accA, float* accB,
+                                              const float* __restrict__ s_ih, int* accA, int* accB,
                                               EndSums& e, const float* x, const float* gy, float* gx, int64_t m)
 {
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
@@ -316,7 +361,21 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
     }
     for (int64_t q = p.nvec * 4 + tid; q < m; q += nthr)
         gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, e, p, copy);
-    flush_hot(accA, accB, hot, p.lanes, lane);  // every lane of the warp gets here
+    flush_hot(accA, accB, hot, p, lane);  // every lane of the warp gets here
+}
+
+// The CTA's fixed-point exponent F: the mean binary exponent of the nonzero
+// finite |gy| among the first vector of each of its threads (a geometric
+// mean, so that a few outliers do not coarsen the unit of the typical
+// terms), placed so that a term of that size is ~2^22 units.
+constexpr int kFixTypicalBits = 23;
+
+__device__ __forceinline__ void exponent_stats(float g, int& esum, int& ecnt)
+{
+    const uint32_t e = (__float_as_uint(g) >> 23) & 0xffu;
+    const bool ok = e != 0u && e != 0xffu;  // zero, subnormal, inf, NaN: no vote
+    esum += ok ? (int)e - 127 : 0;
+    ecnt += ok ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, const float* x, const float* gy,
@@ -327,9 +386,15 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     // this lane's record copy: srec[c << rep_shift] is copy (lane mod R) of record c
     const float4* srec = s_dyn + (threadIdx.x & (R - 1));
     float* s_ih = reinterpret_cast<float*>(s_dyn + (size_t)args.n_smem * R);
-    float* accA = s_ih + (args.N + 2);
-    float* accB = accA + (size_t)(args.N + 2) * args.lanes;
+    int* accA = reinterpret_cast<int*>(s_ih + (args.N + 2));
+    int* accB = accA + (size_t)(args.N + 2) * args.lanes;
+    int* s_exp = accB + (size_t)(args.N + 2) * args.lanes;  // exponent sum and count
     BwdArgs p = args;
+    const int W = 2 * (p.N + 2);
+    float* row = partials + (size_t)blockIdx.x * W;
+    p.rowA = row;
+    p.rowB = row + (p.N + 2);
+    if (threadIdx.x == 0) s_exp[0] = s_exp[1] = 0;
     const int n_chain = p.hdr->n_chain_b;
     p.max_chain = p.hdr->max_chain_b;
     p.n_smem = min(p.K + n_chain, p.n_smem);
@@ -338,8 +403,39 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     for (int i = threadIdx.x; i < (p.n_smem << p.rep_shift); i += blockDim.x)
         s_dyn[i] = __ldg(p.rec + (i >> p.rep_shift));
     for (int i = threadIdx.x; i < p.N + 2; i += blockDim.x) s_ih[i] = p.inv_h[i];
-    for (int i = threadIdx.x; i < 2 * (p.N + 2) * p.lanes; i += blockDim.x) accA[i] = 0.0f;
+    for (int i = threadIdx.x; i < W * p.lanes; i += blockDim.x) accA[i] = 0;
+    // the row collects the FP32 terms and the wraps during the pass
+    for (int i = threadIdx.x; i < W; i += blockDim.x) row[i] = 0.0f;
+    int esum = 0, ecnt = 0;
+    {
+        // the first vector (or query) this thread will process
+        const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (p.nvec > 0) {
+            if (tid < p.nvec) {
+                const float4 g4 = __ldg(reinterpret_cast<const float4*>(gy) + tid);
+                exponent_stats(g4.x, esum, ecnt);
+                exponent_stats(g4.y, esum, ecnt);
+                exponent_stats(g4.z, esum, ecnt);
+                exponent_stats(g4.w, esum, ecnt);
+            }
+        } else if (tid < m) {
+            exponent_stats(__ldg(gy + tid), esum, ecnt);
+        }
+    }
+    esum = __reduce_add_sync(0xffffffffu, esum);
+    ecnt = __reduce_add_sync(0xffffffffu, ecnt);
+    __syncthreads();  // s_exp zeroed, staging done
+    if ((threadIdx.x & 31) == 0 && ecnt > 0) {
+        atomicAdd(&s_exp[0], esum);
+        atomicAdd(&s_exp[1], ecnt);
+    }
     __syncthreads();
+    const int n_exp = s_exp[1];
+    const int e_mean = n_exp > 0 ? (int)floorf((float)s_exp[0] / (float)n_exp) : 0;
+    const int F = min(max(kFixTypicalBits - e_mean, -60), 100);
+    p.scale = __int_as_float((F + 127) << 23);       // 2^F
+    p.wrap = __int_as_float((32 - F + 127) << 23);   // 2^(32-F)
+    const float unit = __int_as_float((127 - F) << 23);  // 2^-F
     EndSums e{0.0f, 0.0f, 0.0f, 0.0f};
     if (n_chain == 0)
         backward_body<false>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
@@ -351,21 +447,22 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
         e.at_a += __shfl_xor_sync(0xffffffffu, e.at_a, o);
         e.at_b += __shfl_xor_sync(0xffffffffu, e.at_b, o);
     }
-    if ((threadIdx.x & 31) == 0) {  // into copy 0
-        atomicAdd(accA, e.clamped_left);
-        atomicAdd(accA + (size_t)(p.N + 1) * p.lanes, e.clamped_right);
-        atomicAdd(accA + p.lanes, e.at_a);
-        atomicAdd(accB + (size_t)p.N * p.lanes, e.at_b);
+    if ((threadIdx.x & 31) == 0) {  // FP32 terms of the row
+        if (e.clamped_left != 0.0f) atomicAdd(p.rowA, e.clamped_left);
+        if (e.clamped_right != 0.0f) atomicAdd(p.rowA + p.N + 1, e.clamped_right);
+        if (e.at_a != 0.0f) atomicAdd(p.rowA + 1, e.at_a);
+        if (e.at_b != 0.0f) atomicAdd(p.rowB + p.N, e.at_b);
     }
-    __syncthreads();
-    // one warp per bin sums its copies (A bins, then B bins: bin k's copies
-    // are acc[k lanes .. k lanes + lanes - 1])
-    float* row = partials + (size_t)blockIdx.x * 2 * (p.N + 2);
-    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int k = threadIdx.x >> 5; k < 2 * (p.N + 2); k += nwarps) {
-        float v = lane < p.lanes ? accA[(size_t)k * p.lanes + lane] : 0.0f;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) row[k] = v;
+    __syncthreads();  // every shared add and every FP32 add to the row done
+    // entry k of the row: its copies summed in 64-bit integers (thread k
+    // starts at copy k mod L, so that a warp's reads spread over the banks),
+    // times 2^-F, plus the FP32 terms and wraps gathered in the row (read at
+    // the L2, where the reductions were performed)
+    for (int k = threadIdx.x; k < W; k += blockDim.x) {
+        long long v = 0;
+        const int* a = accA + (size_t)k * p.lanes;
+        for (int c = 0; c < p.lanes; ++c) v += a[(c + k) & (p.lanes - 1)];
+        row[k] = __fmaf_rn((float)v, unit, __ldcg(row + k));
     }
 }
 

@@ -44,23 +44,25 @@ void choose_cells(pwl_table t, float hmin, int64_t requested);
 pwl_status refresh_texture(pwl_table t, cudaStream_t s);
 
 // Backward: K_b + reserved chain records, N+2 reciprocal lengths and
-// 2 (N+2) FP32 accumulators per copy.  The accumulators have L copies (lane l
+// 2 (N+2) int32 accumulators per copy.  The accumulators have L copies (lane l
 // of every warp adds into copy l mod L, accumulator (i, copy) at i L + copy,
 // so that one warp's atomics spread over L bank classes and never share an
 // address within a copy group): L = 32, 16, 8, 4, 2 or 1, the largest that
 // fits next to all the records.  Chain records beyond the reserve are read
 // from global memory.
+// (plus 16 bytes after the accumulators for the kernel's two scalars)
+constexpr size_t kBwdScalarSmem = 16;
 inline int backward_lanes(const pwl_table_s* t)
 {
     const size_t optin = device_info().smem_optin;
     const size_t rec = 16 * (size_t)(t->Kb + t->chain_reserve_b), n2 = (size_t)(t->N + 2);
     for (int L = 32; L > 1; L /= 2)
-        if (rec + 4 * n2 + 8 * n2 * (size_t)L <= optin) return L;
+        if (rec + 4 * n2 + 8 * n2 * (size_t)L + kBwdScalarSmem <= optin) return L;
     return 1;
 }
 inline size_t backward_fixed_smem(const pwl_table_s* t)
 {
-    return (4 + 8 * (size_t)backward_lanes(t)) * (size_t)(t->N + 2);
+    return (4 + 8 * (size_t)backward_lanes(t)) * (size_t)(t->N + 2) + kBwdScalarSmem;
 }
 // Record copies R (1, 2, 4 or 8; the largest that fits next to the
 // accumulators with every record staged).  A warp's 16-byte gathers are served
