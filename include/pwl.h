@@ -348,8 +348,10 @@ pwl_status pwl_direct_synthetic(const pwl_func* f, int32_t method, uint32_t seed
  * CTA accumulates the per-interval sums in 32-bit fixed point with integer
  * shared-memory atomics: its unit is 2^-F with 2^F ~ 2^23 / (geometric mean
  * of the |gy| among its first queries), each term is rounded to the unit
- * once (absolute error <= 2^-(F+1)), integer wraps are counted exactly, and
- * terms of 2^31 units or more (or inf, NaN) are summed in FP32 instead.  The
+ * once (absolute error <= 2^-(F+1)), integer wraps and multiples of 2^32
+ * units are counted exactly (in FP32 multiples of 2^(32-F), exact below
+ * 2^24 of them per CTA and interval), and terms of 2^62 units or more (or
+ * inf, NaN) are summed in FP32.  The
  * CTA partial sums are then reduced in a fixed order in FP64; run-to-run
  * differences come only from the order of the FP32-summed terms (none for
  * gradients of moderate range).  gx may alias gy.

@@ -26,9 +26,11 @@
 // wrap modulo 2^32, and the lane whose add wraps (seen from the old value
 // the atomic returns: exactly one lane per wrap) adds +-2^32 units to the
 // CTA's row in global memory, so every sum is exact in integer arithmetic
-// whatever the order of the adds.  Terms of 2^31 units or more (and inf,
-// NaN) are added to the row as FP32 instead (global FP32 reductions are
-// native).
+// whatever the order of the adds.  A term of 2^31 units or more adds its low
+// 32 bits the same way and its multiple of 2^32 units to the row (exact in
+// FP32 while the row holds fewer than 2^24 such multiples); only terms
+// beyond 2^62 units, inf and NaN are summed in FP32 (global FP32
+// reductions are native).
 // Pass 2: 32 knots per CTA, the CTA rows split over 16 thread groups, sums
 // the rows in a fixed order (FP64) and forms g_v and g_x (the in-CTA integer
 // sums do not depend on the order of the adds; the few FP32 terms of a row
@@ -71,9 +73,29 @@ struct BwdArgs {
     float* rowB;
 };
 
-// Fixed-point add of the scaled term vs = v 2^F into a shared accumulator:
-// one native atomic, a wrap reported to the row as +-2^(32-F); terms outside
-// the int32 range (and inf, NaN) go to the row as FP32.
+// Fixed-point add of a scaled term vs = v 2^F of any size: T = rint(vs) as
+// a 64-bit integer is split into its low 32 bits r (signed), added to the
+// shared accumulator, and q = (T - r) / 2^32, which goes with the wrap of
+// that add (if any) to the row as q 2^(32-F) (a multiple of 2^32 units:
+// FP32 sums such multiples exactly while the row holds fewer than 2^24 of
+// them).  Terms beyond 2^62 units, inf and NaN go to the row as FP32.
+__device__ __forceinline__ void fix_add_wide(int* acc, float* grow, float vs, float v, float wrap)
+{
+    if (fabsf(vs) < 0x1p62f) {
+        const long long T = __float2ll_rn(vs);
+        const int r = (int)(unsigned)(unsigned long long)T;
+        long long q = (T - (long long)r) >> 32;
+        const int old = atomicAdd(acc, r);
+        const int nw = (int)((unsigned)old + (unsigned)r);
+        if (((old ^ nw) & ~(old ^ r)) < 0) q += r < 0 ? -1 : 1;
+        if (q != 0) atomicAdd(grow, (float)q * wrap);
+    } else {
+        atomicAdd(grow, v);
+    }
+}
+
+// The common case of fix_add_wide: |vs| < 2^31, one native atomic, a wrap
+// reported to the row as +-2^(32-F).
 __device__ __forceinline__ void fix_add(int* acc, float* grow, float vs, float v, float wrap)
 {
     if (fabsf(vs) < 0x1p31f) {
@@ -82,7 +104,7 @@ __device__ __forceinline__ void fix_add(int* acc, float* grow, float vs, float v
         const int nw = (int)((unsigned)old + (unsigned)t);
         if (((old ^ nw) & ~(old ^ t)) < 0) atomicAdd(grow, t < 0 ? -wrap : wrap);
     } else {
-        atomicAdd(grow, v);
+        fix_add_wide(acc, grow, vs, v, wrap);
     }
 }
 
@@ -145,8 +167,8 @@ __device__ __forceinline__ float bwd_query(float x, float g, const float4* __res
 }
 
 // A query's two sums into its lane's accumulator copy: both terms share the
-// range check (|ca| + |cb| = |gy|), the rare out-of-range query adds both to
-// the row as FP32
+// range check (|ca| + |cb| = |gy|); the rare query outside it takes the wide
+// path for both
 __device__ __forceinline__ void bwd_scatter(int* accA, int* accB, int bin, float ca, float cb, const BwdArgs& p,
                                             int copy)
 {
@@ -160,8 +182,8 @@ __device__ __forceinline__ void bwd_scatter(int* accA, int* accB, int bin, float
             if (((oa ^ na) & ~(oa ^ ta)) < 0) atomicAdd(p.rowA + bin, ta < 0 ? -p.wrap : p.wrap);
             if (((ob ^ nb) & ~(ob ^ tb)) < 0) atomicAdd(p.rowB + bin, tb < 0 ? -p.wrap : p.wrap);
         } else {
-            atomicAdd(p.rowA + bin, ca);
-            atomicAdd(p.rowB + bin, cb);
+            fix_add_wide(accA + bin * p.lanes + copy, p.rowA + bin, sa, ca, p.wrap);
+            fix_add_wide(accB + bin * p.lanes + copy, p.rowB + bin, sb, cb, p.wrap);
         }
     }
 }

@@ -308,6 +308,86 @@ def test_backward_matches_oracle(pwl, workloads, name, N):
     t.close()
 
 
+def _backward_vs_oracle(t, xk, vk, x, gy, N):
+    gv = torch.zeros(N + 1, device="cuda")
+    gk = torch.zeros(N + 1, device="cuda")
+    gx = t.backward(x, gy, None, gv, gk)
+    rgx, rgv, rgk, rgva, rgka = oracle.evaluate_grad(xk, vk, x.cpu().numpy().astype(np.float64),
+                                                     gy.cpu().numpy().astype(np.float64))
+    return gx.cpu().numpy(), gv.cpu().numpy(), gk.cpu().numpy(), (rgx, rgv, rgk, rgva, rgka)
+
+
+@pytest.mark.parametrize("N", [1, 5, 4096])
+def test_backward_fixed_point_wraps_and_wide_terms(pwl, workloads, N):
+    # The in-CTA sums are int32 fixed point whose unit each CTA takes from
+    # the |gy| of its first vectors.  Tiny gradients there and O(1) ones
+    # after them put later terms at up to ~2^31 units: most adds wrap (their
+    # +-2^32 units go to the CTA row) and the largest terms leave the int32
+    # range (FP32 path); runs of one sign drive the wraps both ways.
+    f = workloads.GAUSSIAN
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 22) + 5
+    x = workloads.uniform_queries(f, m, seed=3)
+    g = torch.Generator(device="cuda").manual_seed(8)
+    sign = torch.where(torch.arange(m, device="cuda") // 50000 % 2 == 0, 1.0, -1.0)
+    gy = sign * (0.5 + torch.rand(m, generator=g, device="cuda"))
+    gy[: 1 << 20] *= 2.0 ** -9
+    gx, gv, gk, (rgx, rgv, rgk, rgva, rgka) = _backward_vs_oracle(t, xk, vk, x, gy, N)
+    assert np.abs(gx - rgx).max() <= EVAL_REL * np.abs(rgx).max()
+    assert np.all(np.abs(gv - rgv) <= GRAD_REL * rgva + 1e-30)
+    assert np.all(np.abs(gk - rgk) <= GRAD_REL * rgka + 1e-30)
+    t.close()
+
+
+@pytest.mark.parametrize("N", [5, 1024])
+def test_backward_gradients_spanning_many_decades(pwl, workloads, N):
+    # |gy| log-uniform over 1e-15 .. 1e15: the fixed-point unit follows the
+    # geometric mean, the large terms take the FP32 path, the tiny ones round
+    # to a unit that is far below the knots' sums of |terms|
+    f = workloads.LORENTZIAN
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 20) + 3
+    x = workloads.uniform_queries(f, m, seed=4)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    mag = 10.0 ** (30.0 * torch.rand(m, generator=g, device="cuda") - 15.0)
+    gy = (workloads.upstream_grad((m,), seed=6).sign() * mag).float()
+    gx, gv, gk, (rgx, rgv, rgk, rgva, rgka) = _backward_vs_oracle(t, xk, vk, x, gy, N)
+    assert np.all(np.abs(gx - rgx) <= 2.0 ** -23 * np.abs(rgx) + 1e-37)
+    assert np.all(np.abs(gv - rgv) <= GRAD_REL * rgva + 1e-30)
+    assert np.all(np.abs(gk - rgk) <= GRAD_REL * rgka + 1e-30)
+    t.close()
+
+
+def test_backward_zero_and_non_finite_gradients(pwl, workloads):
+    f = workloads.GAUSSIAN
+    N = 256
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 18) + 1
+    x = workloads.uniform_queries(f, m, seed=2)
+    # all-zero upstream gradient: every output exactly zero
+    gx, gv, gk, _ = _backward_vs_oracle(t, xk, vk, x, torch.zeros(m, device="cuda"), N)
+    assert not gx.any() and not gv.any() and not gk.any()
+    # one inf and one NaN among normal gradients, at queries strictly inside
+    # intervals: the knots of those intervals become non-finite like the
+    # FP64 reference, every other knot keeps its value
+    gy = workloads.upstream_grad((m,), seed=5)
+    xs = x.cpu().numpy().astype(np.float64)
+    i = np.clip(np.searchsorted(xk, xs, side="right"), 1, N)
+    inside = np.flatnonzero((xs > xk[i - 1]) & (xs < xk[i]))
+    q_inf, q_nan = int(inside[1000]), int(inside[-1000])
+    gy[q_inf] = float("inf")
+    gy[q_nan] = float("nan")
+    gx, gv, gk, (rgx, rgv, rgk, rgva, rgka) = _backward_vs_oracle(t, xk, vk, x, gy, N)
+    for got, ref, refa in ((gv, rgv, rgva), (gk, rgk, rgka)):
+        fin = np.isfinite(ref)
+        assert not fin.all()
+        assert np.array_equal(np.isfinite(got), fin)
+        assert np.array_equal(np.isnan(got), np.isnan(ref))
+        assert np.all(np.abs(got[fin] - ref[fin]) <= GRAD_REL * refa[fin] + 1e-30)
+    assert np.isinf(gx[q_inf]) and np.isnan(gx[q_nan])
+    t.close()
+
+
 def _sorted_and_clustered_sets(xk, m, g):
     """Query sets whose warps fall in one or two intervals (the warp-aggregated
     scatter) next to warps that do not: sorted uniform queries, one interval,
