@@ -121,18 +121,18 @@ struct EndSums {
 // the side come from selects.  An interior query returns its interval in
 // `bin` and its two sums gy (1 - delta), gy delta in ca, cb; any other query
 // returns bin = -1 (the ends are summed in registers).
-template <bool CHAINS>
+template <bool CHAINS, bool STAGED>
 __device__ __forceinline__ float bwd_query(float x, float g, const float4* __restrict__ srec,
                                            const float* __restrict__ s_ih, EndSums& e, const BwdArgs& p, int& bin,
                                            float& ca, float& cb)
 {
     const float xc = fminf(fmaxf(x, p.a), p.b);  // NaN -> a
     const int c = cell_of(xc, p.inv_w, p.off, p.K);
-    float4 r = (c < p.n_smem) ? srec[c << p.rep_shift] : __ldg(p.rec + c);
+    float4 r = (STAGED || c < p.n_smem) ? srec[c << p.rep_shift] : __ldg(p.rec + c);
     if (CHAINS) {
         for (int it = 0; it < p.max_chain && xc >= r.x && is_link(r.w); ++it) {
             const int j = link_index(r.w);
-            r = (j < p.n_smem) ? srec[j << p.rep_shift] : __ldg(p.rec + j);
+            r = (STAGED || j < p.n_smem) ? srec[j << p.rep_shift] : __ldg(p.rec + j);
         }
     }
     const uint32_t jy = __float_as_uint(r.y);
@@ -172,30 +172,32 @@ __device__ __forceinline__ float bwd_query(float x, float g, const float4* __res
 __device__ __forceinline__ void bwd_scatter(int* accA, int* accB, int bin, float ca, float cb, const BwdArgs& p,
                                             int copy)
 {
-    if (bin >= 0) {
-        const float sa = ca * p.scale, sb = cb * p.scale;
-        if (fabsf(sa) + fabsf(sb) < 0x1p31f) {
-            const int ta = __float2int_rn(sa), tb = __float2int_rn(sb);
-            const int oa = atomicAdd(accA + bin * p.lanes + copy, ta);
-            const int ob = atomicAdd(accB + bin * p.lanes + copy, tb);
-            const int na = (int)((unsigned)oa + (unsigned)ta), nb = (int)((unsigned)ob + (unsigned)tb);
-            if (((oa ^ na) & ~(oa ^ ta)) < 0) atomicAdd(p.rowA + bin, ta < 0 ? -p.wrap : p.wrap);
-            if (((ob ^ nb) & ~(ob ^ tb)) < 0) atomicAdd(p.rowB + bin, tb < 0 ? -p.wrap : p.wrap);
-        } else {
-            fix_add_wide(accA + bin * p.lanes + copy, p.rowA + bin, sa, ca, p.wrap);
-            fix_add_wide(accB + bin * p.lanes + copy, p.rowB + bin, sb, cb, p.wrap);
+    const float sa = ca * p.scale, sb = cb * p.scale;
+    if (bin >= 0 && fabsf(sa) + fabsf(sb) < 0x1p31f) {
+        const int ta = __float2int_rn(sa), tb = __float2int_rn(sb);
+        const int oa = atomicAdd(accA + bin * p.lanes + copy, ta);
+        const int ob = atomicAdd(accB + bin * p.lanes + copy, tb);
+        // sign bit of w: old + t left the int32 range (one branch for both)
+        const int wa = (oa ^ (int)((unsigned)oa + (unsigned)ta)) & ~(oa ^ ta);
+        const int wb = (ob ^ (int)((unsigned)ob + (unsigned)tb)) & ~(ob ^ tb);
+        if ((wa | wb) < 0) {
+            if (wa < 0) atomicAdd(p.rowA + bin, ta < 0 ? -p.wrap : p.wrap);
+            if (wb < 0) atomicAdd(p.rowB + bin, tb < 0 ? -p.wrap : p.wrap);
         }
+    } else if (bin >= 0) {
+        fix_add_wide(accA + bin * p.lanes + copy, p.rowA + bin, sa, ca, p.wrap);
+        fix_add_wide(accB + bin * p.lanes + copy, p.rowB + bin, sb, cb, p.wrap);
     }
 }
 
-template <bool CHAINS>
+template <bool CHAINS, bool STAGED>
 __device__ __forceinline__ float bwd_one(float x, float g, const float4* __restrict__ srec,
                                          const float* __restrict__ s_ih, int* accA, int* accB,
                                          EndSums& e, const BwdArgs& p, int copy)
 {
     int bin;
     float ca, cb;
-    const float gx = bwd_query<CHAINS>(x, g, srec, s_ih, e, p, bin, ca, cb);
+    const float gx = bwd_query<CHAINS, STAGED>(x, g, srec, s_ih, e, p, bin, ca, cb);
     bwd_scatter(accA, accB, bin, ca, cb, p, copy);
     return gx;
 }
@@ -266,7 +268,7 @@ __device__ __forceinline__ void bwd_scatter_hot(int* accA, int* accB, int bin, f
 // aggregates: its queries' sums then stay in registers).  Aggregated: the
 // vector's lookups come first, and a vector that spans more intervals falls
 // back to per-lane atomics and switches back.
-template <bool CHAINS>
+template <bool CHAINS, bool STAGED>
 __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float4* __restrict__ srec,
                                                const float* __restrict__ s_ih, int* accA, int* accB,
                                                EndSums& e, const BwdArgs& p, int copy, int lane, bool detect,
@@ -277,22 +279,22 @@ __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float
     if (!agg) {
         float ca, cb;
         if (hot.bin < 0) {
-            o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
+            o.x = bwd_query<CHAINS, STAGED>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
             bwd_scatter(accA, accB, bin[0], ca, cb, p, copy);
-            o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
+            o.y = bwd_query<CHAINS, STAGED>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
             bwd_scatter(accA, accB, bin[1], ca, cb, p, copy);
-            o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
+            o.z = bwd_query<CHAINS, STAGED>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
             bwd_scatter(accA, accB, bin[2], ca, cb, p, copy);
-            o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
+            o.w = bwd_query<CHAINS, STAGED>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
             bwd_scatter(accA, accB, bin[3], ca, cb, p, copy);
         } else {
-            o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
+            o.x = bwd_query<CHAINS, STAGED>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca, cb);
             bwd_scatter_hot(accA, accB, bin[0], ca, cb, p, copy, hot);
-            o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
+            o.y = bwd_query<CHAINS, STAGED>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca, cb);
             bwd_scatter_hot(accA, accB, bin[1], ca, cb, p, copy, hot);
-            o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
+            o.z = bwd_query<CHAINS, STAGED>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca, cb);
             bwd_scatter_hot(accA, accB, bin[2], ca, cb, p, copy, hot);
-            o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
+            o.w = bwd_query<CHAINS, STAGED>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca, cb);
             bwd_scatter_hot(accA, accB, bin[3], ca, cb, p, copy, hot);
         }
         if (detect) {
@@ -307,10 +309,10 @@ __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float
         return o;
     }
     float ca[4], cb[4];
-    o.x = bwd_query<CHAINS>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca[0], cb[0]);
-    o.y = bwd_query<CHAINS>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca[1], cb[1]);
-    o.z = bwd_query<CHAINS>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca[2], cb[2]);
-    o.w = bwd_query<CHAINS>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca[3], cb[3]);
+    o.x = bwd_query<CHAINS, STAGED>(xv.x, gv.x, srec, s_ih, e, p, bin[0], ca[0], cb[0]);
+    o.y = bwd_query<CHAINS, STAGED>(xv.y, gv.y, srec, s_ih, e, p, bin[1], ca[1], cb[1]);
+    o.z = bwd_query<CHAINS, STAGED>(xv.z, gv.z, srec, s_ih, e, p, bin[2], ca[2], cb[2]);
+    o.w = bwd_query<CHAINS, STAGED>(xv.w, gv.w, srec, s_ih, e, p, bin[3], ca[3], cb[3]);
     agg = warp_two_bins(bin, bF, bL);
     if (agg) {
         float aF = 0.0f, bFs = 0.0f, aL = 0.0f, bLs = 0.0f;
@@ -343,7 +345,7 @@ __device__ __forceinline__ float4 bwd_vec_warp(float4 xv, float4 gv, const float
     return o;
 }
 
-template <bool CHAINS>
+template <bool CHAINS, bool STAGED>
 __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __restrict__ srec,
                                               const float* __restrict__ s_ih, int* accA, int* accB,
                                               EndSums& e, const float* x, const float* gy, float* gx, int64_t m)
@@ -369,36 +371,27 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
         }
 #pragma unroll
         for (int u = 0; u < kBwdUnroll; ++u)
-            __stcs(ov + i + u * nthr, bwd_vec_warp<CHAINS>(xs[u], gs[u], srec, s_ih, accA, accB, e, p, copy, lane,
+            __stcs(ov + i + u * nthr, bwd_vec_warp<CHAINS, STAGED>(xs[u], gs[u], srec, s_ih, accA, accB, e, p, copy, lane,
                                                                u == kBwdUnroll - 1, agg, hot));
     }
     for (; i < p.nvec; i += nthr) {
         const float4 xs = __ldcs(xv + i), gs = __ldcs(gv + i);
         float4 o;
-        o.x = bwd_one<CHAINS>(xs.x, gs.x, srec, s_ih, accA, accB, e, p, copy);
-        o.y = bwd_one<CHAINS>(xs.y, gs.y, srec, s_ih, accA, accB, e, p, copy);
-        o.z = bwd_one<CHAINS>(xs.z, gs.z, srec, s_ih, accA, accB, e, p, copy);
-        o.w = bwd_one<CHAINS>(xs.w, gs.w, srec, s_ih, accA, accB, e, p, copy);
+        o.x = bwd_one<CHAINS, STAGED>(xs.x, gs.x, srec, s_ih, accA, accB, e, p, copy);
+        o.y = bwd_one<CHAINS, STAGED>(xs.y, gs.y, srec, s_ih, accA, accB, e, p, copy);
+        o.z = bwd_one<CHAINS, STAGED>(xs.z, gs.z, srec, s_ih, accA, accB, e, p, copy);
+        o.w = bwd_one<CHAINS, STAGED>(xs.w, gs.w, srec, s_ih, accA, accB, e, p, copy);
         __stcs(ov + i, o);
     }
     for (int64_t q = p.nvec * 4 + tid; q < m; q += nthr)
-        gx[q] = bwd_one<CHAINS>(x[q], gy[q], srec, s_ih, accA, accB, e, p, copy);
+        gx[q] = bwd_one<CHAINS, STAGED>(x[q], gy[q], srec, s_ih, accA, accB, e, p, copy);
     flush_hot(accA, accB, hot, p, lane);  // every lane of the warp gets here
 }
 
-// The CTA's fixed-point exponent F: the mean binary exponent of the nonzero
-// finite |gy| among the first vector of each of its threads (a geometric
-// mean, so that a few outliers do not coarsen the unit of the typical
-// terms), placed so that a term of that size is ~2^22 units.
-constexpr int kFixTypicalBits = 23;
-
-__device__ __forceinline__ void exponent_stats(float g, int& esum, int& ecnt)
-{
-    const uint32_t e = (__float_as_uint(g) >> 23) & 0xffu;
-    const bool ok = e != 0u && e != 0xffu;  // zero, subnormal, inf, NaN: no vote
-    esum += ok ? (int)e - 127 : 0;
-    ecnt += ok ? 1 : 0;
-}
+// The CTA's fixed-point unit comes from the mean binary exponent of the
+// nonzero finite |gy| among the first vector of each of its threads (a
+// geometric mean, so that a few outliers do not coarsen the unit of the
+// typical terms).
 
 __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, const float* x, const float* gy,
                                                         float* gx, int64_t m, float* partials)
@@ -452,17 +445,20 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
         atomicAdd(&s_exp[1], ecnt);
     }
     __syncthreads();
-    const int n_exp = s_exp[1];
-    const int e_mean = n_exp > 0 ? (int)floorf((float)s_exp[0] / (float)n_exp) : 0;
-    const int F = min(max(kFixTypicalBits - e_mean, -60), 100);
-    p.scale = __int_as_float((F + 127) << 23);       // 2^F
-    p.wrap = __int_as_float((32 - F + 127) << 23);   // 2^(32-F)
-    const float unit = __int_as_float((127 - F) << 23);  // 2^-F
+    const int F = fix_exponent(s_exp[0], s_exp[1]);
+    p.scale = exp2_int(F);          // 2^F
+    p.wrap = exp2_int(32 - F);      // 2^(32-F)
+    const float unit = exp2_int(-F);  // 2^-F
     EndSums e{0.0f, 0.0f, 0.0f, 0.0f};
-    if (n_chain == 0)
-        backward_body<false>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
-    else
-        backward_body<true>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
+    // every record in shared memory (the usual case): no global-record branch per lookup
+    const bool staged = p.n_smem >= p.K + n_chain;
+    if (n_chain == 0) {
+        if (staged) backward_body<false, true>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
+        else backward_body<false, false>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
+    } else {
+        if (staged) backward_body<true, true>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
+        else backward_body<true, false>(p, srec, s_ih, accA, accB, e, x, gy, gx, m);
+    }
     for (int o = 16; o > 0; o >>= 1) {
         e.clamped_left += __shfl_xor_sync(0xffffffffu, e.clamped_left, o);
         e.clamped_right += __shfl_xor_sync(0xffffffffu, e.clamped_right, o);

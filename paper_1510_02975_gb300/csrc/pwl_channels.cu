@@ -606,7 +606,8 @@ size_t channels_smem_bytes(int64_t N, int64_t K, bool backward)
 int64_t channels_default_cells(int64_t N, bool backward)
 {
     // 4 (N+1) cells forward, 2 (N+1) backward, as far as one CTA's shared memory allows
-    const size_t budget = device_info().smem_optin - sizeof(float) * 256;  // static tile parameters
+    // the static tile parameters of the kernel share the CTA's shared memory
+    const size_t budget = device_info().smem_optin - (backward ? sizeof(TileParams) : sizeof(TileParamsF));
     int64_t K = (backward ? 2 : 4) * (N + 1);
     while (K > 16 && channels_smem_bytes(N, K, backward) > budget) K -= 16;
     return K;
@@ -620,7 +621,7 @@ pwl_status channels_launch(const ChanArgs& base, bool backward, int io_dtype, co
     const DeviceInfo& di = device_info();
     const int tile_ch = backward ? kCh : kChF;       // channels per tile
     const int cluster_ctas = backward ? 2 : kClF;    // CTAs per cluster (adjacent tiles, same rows)
-    if (smem > di.smem_optin)
+    if (smem + (backward ? sizeof(TileParams) : sizeof(TileParamsF)) > di.smem_optin)
         return fail(PWL_ENOTSUP, "channel index of %zu bytes (%d channels x %d cells, N = %d) does not fit one CTA",
                     smem, tile_ch, p.K, p.N);
     p.tiles = (p.C + tile_ch - 1) / tile_ch;
