@@ -423,18 +423,19 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     for (int i = threadIdx.x; i < W; i += blockDim.x) row[i] = 0.0f;
     int esum = 0, ecnt = 0;
     {
-        // the first vector (or query) this thread will process
+        // the first vector (or query) this thread will process (read at the
+        // L2, not through the read-only path: gx may alias gy)
         const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (p.nvec > 0) {
             if (tid < p.nvec) {
-                const float4 g4 = __ldg(reinterpret_cast<const float4*>(gy) + tid);
+                const float4 g4 = __ldcg(reinterpret_cast<const float4*>(gy) + tid);
                 exponent_stats(g4.x, esum, ecnt);
                 exponent_stats(g4.y, esum, ecnt);
                 exponent_stats(g4.z, esum, ecnt);
                 exponent_stats(g4.w, esum, ecnt);
             }
         } else if (tid < m) {
-            exponent_stats(__ldg(gy + tid), esum, ecnt);
+            exponent_stats(__ldcg(gy + tid), esum, ecnt);
         }
     }
     esum = __reduce_add_sync(0xffffffffu, esum);
