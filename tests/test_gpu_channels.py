@@ -85,6 +85,43 @@ def test_channels_forward_bf16_io(pwl):
     assert np.all(np.abs(got - ref) <= 2.0**-8 * np.abs(ref) * 1.0001 + EVAL_REL * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("io", ["fp32", "bf16"])
+def test_channels_forward_aligned_and_unaligned_x_agree(pwl, io):
+    # the same x at a 16-byte aligned base and at a base 2 or 4 bytes off:
+    # the same y bit for bit, and the oracle's values on a partial last tile
+    # (44 channels: 4 past the last full 8-channel tile), ragged rows (5003),
+    # NaN, clamped and at-knot queries.
+    C, N, R = 44, 256, 5003
+    knots, values = _channel_tables(pwl, C, N, seed=7)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    x = torch.randn(R, C, generator=g, device="cuda") * 2.0
+    x[0, :] = float("nan")
+    x[1, :] = 9.0
+    x[2, :] = -9.0
+    x[3, :] = torch.tensor(knots[:, N // 3], device="cuda")
+    if io == "bf16":
+        x = x.to(torch.bfloat16)
+    kt, vt = torch.tensor(knots, device="cuda"), torch.tensor(values, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y1 = pwl.pwl_channels_forward(kt, vt, x, status=st)
+    buf = torch.empty(R * C + 1, dtype=x.dtype, device="cuda")
+    xu = buf[1:].view(R, C)
+    xu.copy_(x)
+    assert xu.data_ptr() % 16 != 0
+    y2 = pwl.pwl_channels_forward(kt, vt, xu, status=st)
+    assert int(st.item()) == 0
+    assert torch.equal(torch.isnan(y1), torch.isnan(y2))
+    assert torch.equal(torch.nan_to_num(y1), torch.nan_to_num(y2))
+    ref = _oracle_rows(knots, values, x.float().cpu().numpy().astype(np.float64))
+    got = y1.float().cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.isnan(ref), np.isnan(got))
+    ok = ~np.isnan(ref)
+    if io == "fp32":
+        assert np.abs(got[ok] - ref[ok]).max() <= EVAL_REL * np.abs(ref[ok]).max()
+    else:
+        assert np.all(np.abs(got[ok] - ref[ok]) <= 2.0**-8 * np.abs(ref[ok]) * 1.0001 + EVAL_REL * np.abs(ref[ok]).max())
+
+
 def test_channels_non_increasing_knots_flagged(pwl):
     C, N = 16, 8
     knots = np.tile(np.linspace(-1, 1, N + 1), (C, 1)).astype(np.float32)
