@@ -97,11 +97,6 @@ __device__ __forceinline__ void cp_async16(void* dst_smem, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
 }
-// 8 bytes (both addresses 8-byte aligned), cached in L1 on the way
-__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
-}
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // Wait until at most N of this thread's committed groups are pending.

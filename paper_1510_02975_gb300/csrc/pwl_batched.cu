@@ -185,7 +185,9 @@ __device__ __forceinline__ void batch_range(const Lookup& d, const float2* P, co
 {
     // 16-byte vectors between the first and the last 16-byte boundary of the
     // range, scalar head and tail (fewer than 4 queries each).  The head and
-    // tail loads go out first and complete while the vectors stream.
+    // tail loads go out first and complete while the vectors stream.  The
+    // vectors are read at the L2 only (ld.global.cg): the staged index leaves
+    // the L1 little room, and no other CTA reads the same lines.
     const int64_t v0 = min(q1, (q0 + 3) & ~(int64_t)3);
     const int64_t v1 = max(v0, q1 & ~(int64_t)3);
     const int nt = blockDim.x;
@@ -199,7 +201,7 @@ __device__ __forceinline__ void batch_range(const Lookup& d, const float2* P, co
     for (; i + (U - 1) * nt < nv; i += U * nt) {
         float4 a[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = __ldcs(xv + i + u * nt);
+        for (int u = 0; u < U; ++u) a[u] = __ldcg(xv + i + u * nt);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             a[u].x = batch_lerp<CHAINS, STAGED>(a[u].x, d, P, S, xk);
@@ -211,7 +213,7 @@ __device__ __forceinline__ void batch_range(const Lookup& d, const float2* P, co
         for (int u = 0; u < U; ++u) __stcs(yv + i + u * nt, a[u]);
     }
     for (; i < nv; i += nt) {
-        float4 a = __ldcs(xv + i);
+        float4 a = __ldcg(xv + i);
         a.x = batch_lerp<CHAINS, STAGED>(a.x, d, P, S, xk);
         a.y = batch_lerp<CHAINS, STAGED>(a.y, d, P, S, xk);
         a.z = batch_lerp<CHAINS, STAGED>(a.z, d, P, S, xk);
@@ -321,14 +323,18 @@ __device__ __forceinline__ void run_staged(const EvalParams& p, const BatchFunc&
 }
 
 // n float2 records from global memory into shared memory by the whole CTA,
-// as 8-byte cp.async copies that use no registers: every thread issues all
-// of its copies (~10 for an average index) before one wait, so staging a
-// function's index costs about one load latency instead of one per THREADS
-// records.  The caller commits, waits and synchronises.
+// as cp.async copies that use no registers: every thread issues all of its
+// copies (~5 for an average index) before one wait, so staging a function's
+// index costs about one load latency instead of one per THREADS records.
+// The copies are 16 bytes (two records) and skip the L1 (cp.async.cg): every
+// function's cell records start 16-byte aligned and both arrays hold an even
+// number of records (K is even).  The caller commits, waits and synchronises.
 template <int THREADS>
 __device__ __forceinline__ void stage_records(float2* dst, const float2* __restrict__ src, int n)
 {
-    for (int i = threadIdx.x; i < n; i += THREADS) cp_async8(dst + i, src + i);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (int i = threadIdx.x; i < n / 2; i += THREADS) cp_async16(d4 + i, s4 + i);
 }
 
 // Staging by the CTA's threads: the SM streams nothing while a CTA copies
