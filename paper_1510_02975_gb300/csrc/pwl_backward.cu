@@ -63,7 +63,7 @@ struct BwdArgs {
     int lanes;          // accumulator copies (a power of two <= 32), lane l adds into copy l mod lanes
     int rep_shift;      // log2 of the record copies R: lane l reads srec[c R + l mod R]
     float a, b, inv_w, off;
-    float s_first, s_last;  // slopes of intervals 1 and N (set by the kernel)
+    float s_last;       // slope of interval N (set by the kernel)
     int64_t nvec;       // float4 vectors (x, gy and gx all 16-byte aligned), else 0
     // set by the kernel: the CTA's fixed-point unit 2^-F (scale = 2^F), the
     // value of one int32 wrap (2^(32-F)) and the CTA's row (A columns at
@@ -108,17 +108,17 @@ __device__ __forceinline__ void fix_add(int* acc, float* grow, float vs, float v
     }
 }
 
-// Queries at or beyond the ends of [a, b] all feed the same four sums; a
-// skewed input (a query set clipped to the domain) can send half of them
-// there, so they are summed in registers and added once per thread at the
-// end instead of through contended shared-memory atomics.
+// Queries beyond the ends of [a, b] and at x = b all feed the same three
+// sums; a skewed input (a query set clipped to the domain) can send half of
+// them there, so they are summed in registers and added once per warp at
+// the end instead of through contended shared-memory atomics.
 struct EndSums {
-    float clamped_left, clamped_right, at_a, at_b;
+    float clamped_left, clamped_right, at_b;
 };
 
 // One query, without branches apart from chain walks: the lookup runs on the
 // clamped point (a NaN looks up a and contributes nothing), the interval and
-// the side come from selects.  An interior query returns its interval in
+// the side come from selects.  A query in [a, b) returns its interval in
 // `bin` and its two sums gy (1 - delta), gy delta in ca, cb; any other query
 // returns bin = -1 (the ends are summed in registers).
 template <bool CHAINS, bool STAGED>
@@ -152,15 +152,16 @@ __device__ __forceinline__ float bwd_query(float x, float g, const float4* __res
     ca = g * one_minus;
     cb = g * delta;
     float gx = g * s;
-    if (!(x > p.a && x < p.b)) {  // the ends, beyond them, NaN: rare in most query sets
+    // x = a needs nothing apart: its lookup is interval 1 at delta = 0 (the
+    // hot-interval registers absorb a point mass there, as in a set clipped
+    // to the domain)
+    if (!(x >= p.a && x < p.b)) {  // beyond the ends, x = b, NaN: rare in most query sets
         bin = -1;
-        // clamped queries feed g_v[0] or g_v[N]; x = a is interval 1 at
-        // delta = 0, x = b interval N at delta = 1
+        // clamped queries feed g_v[0] or g_v[N]; x = b is interval N at delta = 1
         e.clamped_left += x < p.a ? g : 0.0f;
-        e.at_a += x == p.a ? g : 0.0f;
         e.clamped_right += x > p.b ? g : 0.0f;
         e.at_b += x == p.b ? g : 0.0f;
-        gx = x == p.a ? g * p.s_first : (x == p.b ? g * p.s_last : 0.0f);
+        gx = x == p.b ? g * p.s_last : 0.0f;
         gx = x != x ? x : gx;
     }
     return gx;
@@ -413,7 +414,6 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     const int n_chain = p.hdr->n_chain_b;
     p.max_chain = p.hdr->max_chain_b;
     p.n_smem = min(p.K + n_chain, p.n_smem);
-    p.s_first = p.slope[1];
     p.s_last = p.slope[p.N];
     for (int i = threadIdx.x; i < (p.n_smem << p.rep_shift); i += blockDim.x)
         s_dyn[i] = __ldg(p.rec + (i >> p.rep_shift));
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     p.scale = exp2_int(F);          // 2^F
     p.wrap = exp2_int(32 - F);      // 2^(32-F)
     const float unit = exp2_int(-F);  // 2^-F
-    EndSums e{0.0f, 0.0f, 0.0f, 0.0f};
+    EndSums e{0.0f, 0.0f, 0.0f};
     // every record in shared memory (the usual case): no global-record branch per lookup
     const bool staged = p.n_smem >= p.K + n_chain;
     if (n_chain == 0) {
@@ -463,13 +463,11 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, cons
     for (int o = 16; o > 0; o >>= 1) {
         e.clamped_left += __shfl_xor_sync(0xffffffffu, e.clamped_left, o);
         e.clamped_right += __shfl_xor_sync(0xffffffffu, e.clamped_right, o);
-        e.at_a += __shfl_xor_sync(0xffffffffu, e.at_a, o);
         e.at_b += __shfl_xor_sync(0xffffffffu, e.at_b, o);
     }
     if ((threadIdx.x & 31) == 0) {  // FP32 terms of the row
         if (e.clamped_left != 0.0f) atomicAdd(p.rowA, e.clamped_left);
         if (e.clamped_right != 0.0f) atomicAdd(p.rowA + p.N + 1, e.clamped_right);
-        if (e.at_a != 0.0f) atomicAdd(p.rowA + 1, e.at_a);
         if (e.at_b != 0.0f) atomicAdd(p.rowB + p.N, e.at_b);
     }
     __syncthreads();  // every shared add and every FP32 add to the row done

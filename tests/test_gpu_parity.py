@@ -388,6 +388,34 @@ def test_backward_zero_and_non_finite_gradients(pwl, workloads):
     t.close()
 
 
+@pytest.mark.parametrize("N", [256, 4096])
+def test_backward_table_gradients_reproducible(pwl, workloads, N):
+    # Interior queries and gradients of moderate range: the in-CTA sums are
+    # integers (order-independent), the only FP32 terms of a CTA's row are
+    # wraps (exact multiples of the unit's 2^32), each CTA's unit comes from
+    # the same gy values on every call, and the rows are reduced in a fixed
+    # order, so two calls give the same table gradients bit for bit.
+    f = workloads.LORENTZIAN
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 22) + 1
+    x = workloads.uniform_queries(f, m, seed=12)
+    x[x == float(f["a"])] = 0.0  # strictly inside (a, b): no end sums
+    gy = workloads.upstream_grad((m,), seed=13)
+    out = []
+    for _ in range(2):
+        gv, gk = torch.zeros(N + 1, device="cuda"), torch.zeros(N + 1, device="cuda")
+        gx = t.backward(x, gy, None, gv, gk)
+        out.append((gx, gv, gk))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    assert torch.equal(out[0][2], out[1][2])
+    _, rgv, rgk, rgva, rgka = oracle.evaluate_grad(xk, vk, x.cpu().numpy().astype(np.float64),
+                                                   gy.cpu().numpy().astype(np.float64))
+    assert np.all(np.abs(out[0][1].cpu().numpy() - rgv) <= GRAD_REL * rgva + 1e-30)
+    assert np.all(np.abs(out[0][2].cpu().numpy() - rgk) <= GRAD_REL * rgka + 1e-30)
+    t.close()
+
+
 def test_backward_in_place_and_unaligned(pwl, workloads):
     # gx may alias gy: the in-place call gives the out-of-place gx bit for bit
     # (each CTA's fixed-point unit comes from gy values that only the thread
