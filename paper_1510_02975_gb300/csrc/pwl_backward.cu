@@ -15,8 +15,9 @@
 // atomics into up to 32 accumulator copies for random queries, a warp-level
 // sum for vectors that lie in one or two intervals (sorted or clustered
 // queries), and registers for a warp's hot interval (a point mass) and for
-// the queries at or beyond the ends of [a, b].  It then writes its partial
-// sums to the workspace (one row per CTA).
+// the queries beyond the ends of [a, b] and at x = b (x = a is interval 1 at
+// delta = 0, an interior query).  It then writes its partial sums to the
+// workspace (one row per CTA).
 // The shared-memory sums are 32-bit fixed point (FP32 shared-memory atomic
 // adds are a compare-and-swap loop in software; 32-bit integer adds are a
 // single native operation, ~4x the throughput with random bins).  Each CTA
@@ -32,9 +33,11 @@
 // beyond 2^62 units, inf and NaN are summed in FP32 (global FP32
 // reductions are native).
 // Pass 2: 32 knots per CTA, the CTA rows split over 16 thread groups, sums
-// the rows in a fixed order (FP64) and forms g_v and g_x (the in-CTA integer
-// sums do not depend on the order of the adds; the few FP32 terms of a row
-// do, so results are reproducible to their rounding).
+// the rows in a fixed order (FP64) and forms g_v and g_x.  The in-CTA
+// integer sums and the wraps (multiples of 2^32 units) do not depend on the
+// order of the adds; only the FP32 terms of a row (clamped queries, x = b,
+// terms beyond the int32 range) do, so results without those are
+// reproducible bit for bit, the rest to the rounding of those terms.
 #include <math.h>
 
 #include <algorithm>
