@@ -358,6 +358,23 @@ def test_backward_gradients_spanning_many_decades(pwl, workloads, N):
     t.close()
 
 
+def test_backward_unit_from_an_empty_sample(pwl, workloads):
+    # zero gradients in every thread's first vector (no exponent sample: the
+    # default unit 2^-23) and N(0, 1) ones after them
+    f = workloads.BESSEL_J0
+    N = 1024
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 22) + 9
+    x = workloads.uniform_queries(f, m, seed=14)
+    gy = workloads.upstream_grad((m,), seed=15)
+    gy[: 1 << 20] = 0.0
+    gx, gv, gk, (rgx, rgv, rgk, rgva, rgka) = _backward_vs_oracle(t, xk, vk, x, gy, N)
+    assert np.abs(gx - rgx).max() <= EVAL_REL * np.abs(rgx).max()
+    assert np.all(np.abs(gv - rgv) <= GRAD_REL * rgva + 1e-30)
+    assert np.all(np.abs(gk - rgk) <= GRAD_REL * rgka + 1e-30)
+    t.close()
+
+
 def test_backward_zero_and_non_finite_gradients(pwl, workloads):
     f = workloads.GAUSSIAN
     N = 256
