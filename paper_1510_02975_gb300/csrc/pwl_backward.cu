@@ -395,7 +395,28 @@ __device__ __forceinline__ void backward_body(const BwdArgs& p, const float4* __
 // The CTA's fixed-point unit comes from the mean binary exponent of the
 // nonzero finite |gy| among the first vector of each of its threads (a
 // geometric mean, so that a few outliers do not coarsen the unit of the
-// typical terms).
+// typical terms): F = kFixTypicalBits - that mean, so a typical term is
+// ~2^22 units.  exponent_stats adds the binary exponent of a nonzero finite
+// |g| to esum and counts it in ecnt (zero, subnormal, inf and NaN are
+// skipped); with no usable value F = kFixTypicalBits.  F stays inside
+// [-60, 126]: 2^F and 2^-F are normal FP32 numbers, and a term of the wide
+// path (below 2^62 units) carries at most 2^30 multiples of 2^(32-F), which
+// stays below FP32's largest value.  Gradients whose typical magnitude is
+// below 2^-103 (~1e-31) therefore get a unit coarser than 2^-23 of them.
+constexpr int kFixTypicalBits = 23;
+__device__ __forceinline__ void exponent_stats(float g, int& esum, int& ecnt)
+{
+    const uint32_t e = (__float_as_uint(g) >> 23) & 0xffu;
+    const bool ok = e != 0u && e != 0xffu;
+    esum += ok ? (int)e - 127 : 0;
+    ecnt += ok ? 1 : 0;
+}
+__device__ __forceinline__ int fix_exponent(int esum, int ecnt)
+{
+    const int e_mean = ecnt > 0 ? (int)floorf((float)esum / (float)ecnt) : 0;
+    return min(max(kFixTypicalBits - e_mean, -60), 126);
+}
+__device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 127) << 23); }
 
 __global__ void __launch_bounds__(1024) backward_kernel(const BwdArgs args, const float* x, const float* gy,
                                                         float* gx, int64_t m, float* partials)

@@ -400,28 +400,6 @@ __device__ __forceinline__ float clamp_nan(float x, float a, float b)
     return r;
 }
 
-// Fixed-point sums of the backward kernels: the binary exponent of a nonzero
-// finite |g| added to esum and counted in ecnt (zero, subnormal, inf and NaN
-// are skipped); the mean exponent of a sample sets the unit 2^-F of a sum so
-// that a typical term is ~2^22 units (F = kFixTypicalBits - mean exponent).
-constexpr int kFixTypicalBits = 23;
-__device__ __forceinline__ void exponent_stats(float g, int& esum, int& ecnt)
-{
-    const uint32_t e = (__float_as_uint(g) >> 23) & 0xffu;
-    const bool ok = e != 0u && e != 0xffu;
-    esum += ok ? (int)e - 127 : 0;
-    ecnt += ok ? 1 : 0;
-}
-// The exponent F of the unit 2^-F for esum / ecnt (F = kFixTypicalBits when
-// the sample has no usable value), kept inside [-60, 100] so that 2^F, 2^-F
-// and 2^(32-F) are normal FP32 numbers.
-__device__ __forceinline__ int fix_exponent(int esum, int ecnt)
-{
-    const int e_mean = ecnt > 0 ? (int)floorf((float)esum / (float)ecnt) : 0;
-    return min(max(kFixTypicalBits - e_mean, -60), 100);
-}
-__device__ __forceinline__ float exp2_int(int e) { return __int_as_float((e + 127) << 23); }
-
 // Device-side status of a table, written by the build kernels and read by
 // every kernel that uses the table (so that an asynchronous update needs no
 // host round trip).

@@ -375,6 +375,25 @@ def test_backward_unit_from_an_empty_sample(pwl, workloads):
     t.close()
 
 
+@pytest.mark.parametrize("scale", [1e-28, 1e28])
+def test_backward_gradients_of_extreme_magnitude(pwl, workloads, scale):
+    # gy ~ N(0, 1) * 1e-28: the fixed-point unit 2^-117, still 2^-23 of the
+    # typical term; * 1e28: every term is 2^31 units or more and takes the
+    # exact 64-bit split (low 32 bits in shared memory, multiples of 2^32
+    # units in the row)
+    f = workloads.GAUSSIAN
+    N = 1024
+    t, xk, vk = _table_and_ref(pwl, f, N)
+    m = (1 << 21) + 3
+    x = workloads.uniform_queries(f, m, seed=16)
+    gy = workloads.upstream_grad((m,), seed=17) * scale
+    gx, gv, gk, (rgx, rgv, rgk, rgva, rgka) = _backward_vs_oracle(t, xk, vk, x, gy, N)
+    assert np.abs(gx - rgx).max() <= EVAL_REL * np.abs(rgx).max()
+    assert np.all(np.abs(gv - rgv) <= GRAD_REL * rgva)
+    assert np.all(np.abs(gk - rgk) <= GRAD_REL * rgka)
+    t.close()
+
+
 def test_backward_zero_and_non_finite_gradients(pwl, workloads):
     f = workloads.GAUSSIAN
     N = 256
