@@ -347,8 +347,10 @@ pwl_status pwl_direct_synthetic(const pwl_func* f, int32_t method, uint32_t seed
  * g_values / g_knots are accumulated into (the caller zeroes them).  Each
  * CTA accumulates the per-interval sums in 32-bit fixed point with integer
  * shared-memory atomics: its unit is 2^-F with 2^F ~ 2^23 / (geometric mean
- * of the |gy| among its first queries), each term is rounded to the unit
- * once (absolute error <= 2^-(F+1)), integer wraps and multiples of 2^32
+ * of the |gy| among its first queries; F limited to [-60, 126], so that
+ * gradients of typical magnitude below ~1e-31 get a coarser unit), each
+ * term is rounded to the unit once (absolute error <= 2^-(F+1)), integer
+ * wraps and multiples of 2^32
  * units are counted exactly (in FP32 multiples of 2^(32-F), exact below
  * 2^24 of them per CTA and interval), and terms of 2^62 units or more (or
  * inf, NaN) are summed in FP32.  The
