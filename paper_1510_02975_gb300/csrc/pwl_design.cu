@@ -76,15 +76,16 @@ __device__ __forceinline__ double block_exclusive_scan(double v, double* s_warp,
     return r;
 }
 
-// d_k for this thread's cells of the chunk at c0 (sum returned); the
-// sampled path is a template flag, chosen once per chunk
-template <typename T, bool SAMPLED>
+// d_k for this thread's cells of the chunk at c0 (sum returned), THREADS
+// threads per chunk; the sampled path is a template flag, chosen once per
+// chunk
+template <typename T, bool SAMPLED, int THREADS>
 __device__ __forceinline__ double density_chunk(const pwl_func& F, int64_t c0, int64_t M, double delta,
                                                 double* __restrict__ d)
 {
     double acc = 0.0;
-    for (int r = 0; r < kPerThread; ++r) {
-        const int64_t k = c0 + r * kDesignThreads + threadIdx.x;
+    for (int r = 0; r < kChunk / THREADS; ++r) {
+        const int64_t k = c0 + r * THREADS + threadIdx.x;
         if (k < M) {
             // t_k = a + (k + 1/2) delta, rounded as written (no fused multiply-add)
             const double t = __dadd_rn(F.a, __dmul_rn((double)k + 0.5, delta));
@@ -97,10 +98,17 @@ __device__ __forceinline__ double density_chunk(const pwl_func& F, int64_t c0, i
     return acc;
 }
 
+// The density of a single function's few chunks (128 at N = 4096) takes
+// kDensityThreads threads per chunk, so that its FP64 f'' evaluations keep
+// more warps in flight per SM than the scans' 256-thread CTAs would: 512
+// threads (the FP64 J0 path needs ~128 registers, so 1024 would spill
+// heavily) took the bench's design graph of 9 tables from 0.56 to 0.49 ms.
+constexpr int kDensityThreads = 512;
+
 template <typename T, bool SAMPLED>
-__global__ void __launch_bounds__(kDesignThreads) density_chunks_kernel(DesignPlan p)
+__global__ void __launch_bounds__(kDensityThreads) density_chunks_kernel(DesignPlan p)
 {
-    __shared__ double s_red[kDesignThreads / 32];
+    __shared__ double s_red[kDensityThreads / 32];
     for (int64_t ch = blockIdx.x; ch < p.total_chunks; ch += gridDim.x) {
         const int f = find_segment(p.choff, p.F, ch);
         const pwl_func F = p.funcs[f];
@@ -109,13 +117,13 @@ __global__ void __launch_bounds__(kDesignThreads) density_chunks_kernel(DesignPl
         const int64_t c0 = (ch - p.choff[f]) * kChunk;
         const double delta = (F.b - F.a) / (double)M;
         double* __restrict__ d = p.d + p.moff[f];
-        double acc = density_chunk<T, SAMPLED>(F, c0, M, delta, d);
+        double acc = density_chunk<T, SAMPLED, kDensityThreads>(F, c0, M, delta, d);
         acc = warp_sum(acc);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
             double s = 0.0;
-            for (int w = 0; w < kDesignThreads / 32; ++w) s += s_red[w];
+            for (int w = 0; w < kDensityThreads / 32; ++w) s += s_red[w];
             p.csum[ch] = s;
         }
         __syncthreads();
@@ -767,16 +775,16 @@ pwl_status design_launch(const DesignPlan& p, cudaStream_t s)
     const int kinds = plan_kinds(p.kinds);
     if (kinds & kKindsAnalytic) {
         if (p.precision == PWL_PREC_FP32)
-            density_chunks_kernel<float, false><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+            density_chunks_kernel<float, false><<<grid_chunks, kDensityThreads, 0, s>>>(p);
         else
-            density_chunks_kernel<double, false><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+            density_chunks_kernel<double, false><<<grid_chunks, kDensityThreads, 0, s>>>(p);
         PWL_CHECK_LAUNCH("density_chunks_kernel");
     }
     if (kinds & kKindsSampled) {
         if (p.precision == PWL_PREC_FP32)
-            density_chunks_kernel<float, true><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+            density_chunks_kernel<float, true><<<grid_chunks, kDensityThreads, 0, s>>>(p);
         else
-            density_chunks_kernel<double, true><<<grid_chunks, kDesignThreads, 0, s>>>(p);
+            density_chunks_kernel<double, true><<<grid_chunks, kDensityThreads, 0, s>>>(p);
         PWL_CHECK_LAUNCH("density_chunks_kernel");
     }
     chunk_scan_kernel<<<(int)std::min<int64_t>(p.F, 65535), kDesignThreads, 0, s>>>(p);
