@@ -274,6 +274,10 @@ __global__ void __launch_bounds__(64) gram_spike_kernel(ProjectPlan p, const int
 // every row i = 2s-1 (mod 2s) eliminates its couplings to rows i-s and i+s
 // (coefficients a: to i-s, c: to i+s).  One row (s_top - 1) is then
 // uncoupled; back substitution fills rows s-1 (mod 2s) for s = s_top/2..1.
+// One CTA solves one function, so the solve runs on a single SM's FP64
+// pipe: the pivots' reciprocals come from recip_newton (five FP64
+// operations) and the entries from products with 1/6 and 1/3, not from
+// FP64 divisions (the bench's design graph 0.495 -> 0.455 ms).
 __global__ void __launch_bounds__(kSolveThreads) gram_solve_kernel(ProjectPlan p, int use_smem)
 {
     extern __shared__ double s_cr[];
@@ -291,9 +295,9 @@ __global__ void __launch_bounds__(kSolveThreads) gram_solve_kernel(ProjectPlan p
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const double hl = (i > 0) ? x[i] - x[i - 1] : 0.0;
             const double hr = (i < N) ? x[i + 1] - x[i] : 0.0;
-            A[i] = hl / 6.0;
-            B[i] = (hl + hr) / 3.0;
-            C[i] = hr / 6.0;
+            A[i] = hl * (1.0 / 6.0);
+            B[i] = (hl + hr) * (1.0 / 3.0);
+            C[i] = hr * (1.0 / 6.0);
             D[i] = ((i > 0) ? lr[i - 1].y : 0.0) + ((i < N) ? lr[i].x : 0.0);
         }
         __syncthreads();
@@ -301,13 +305,13 @@ __global__ void __launch_bounds__(kSolveThreads) gram_solve_kernel(ProjectPlan p
         for (; 2 * s - 1 < n; s <<= 1) {
             for (int i = 2 * s - 1 + 2 * s * threadIdx.x; i < n; i += 2 * s * blockDim.x) {
                 const int l = i - s, r = i + s;
-                const double alpha = -A[i] / B[l];
+                const double alpha = -A[i] * recip_newton(B[l]);
                 double an = alpha * A[l];
                 double bn = B[i] + alpha * C[l];
                 double dn = D[i] + alpha * D[l];
                 double cn = 0.0;
                 if (r < n) {
-                    const double gamma = -C[i] / B[r];
+                    const double gamma = -C[i] * recip_newton(B[r]);
                     cn = gamma * C[r];
                     bn += gamma * A[r];
                     dn += gamma * D[r];
@@ -319,14 +323,14 @@ __global__ void __launch_bounds__(kSolveThreads) gram_solve_kernel(ProjectPlan p
             }
             __syncthreads();
         }
-        if (threadIdx.x == 0) D[s - 1] = D[s - 1] / B[s - 1];
+        if (threadIdx.x == 0) D[s - 1] = D[s - 1] * recip_newton(B[s - 1]);
         __syncthreads();
         for (s >>= 1; s >= 1; s >>= 1) {
             for (int i = s - 1 + 2 * s * threadIdx.x; i < n; i += 2 * s * blockDim.x) {
                 double v = D[i];
                 if (i - s >= 0) v -= A[i] * D[i - s];
                 if (i + s < n) v -= C[i] * D[i + s];
-                D[i] = v / B[i];
+                D[i] = v * recip_newton(B[i]);
             }
             __syncthreads();
         }
