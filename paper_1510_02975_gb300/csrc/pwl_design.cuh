@@ -8,6 +8,21 @@ namespace pwl {
 
 constexpr int kMaxIntervals = 1048575;
 
+// 1/d for a positive normal FP64 d by Newton's method for the reciprocal,
+// r <- r + r (1 - d r), from the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64); each step doubles the correct bits, two reach FP64
+// rounding.  Five FP64 operations against about twice that for a division
+// (the Gram solves and the table build's slopes and reciprocal lengths).
+__device__ __forceinline__ double recip_newton(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 // F functions; function f owns knots koff[f] .. koff[f+1]-1 (N_f + 1 of them),
 // density cells moff[f] .. moff[f+1]-1 (M_f), chunks choff[f] .. choff[f+1]-1,
 // and G entries moff[f] + f .. moff[f+1] + f (M_f + 1).

@@ -142,19 +142,6 @@ __global__ void hat_integrals_kernel(ProjectPlan p, const __grid_constant__ Gaus
 // The rows are assembled on the fly (M_{i,i-1} = h_i/6, M_ii = (h_i +
 // h_{i+1})/3, M_{i,i+1} = h_{i+1}/6, b_i = R_i + L_{i+1}).  About 20 FP64
 // operations per row, one division; no barrier beyond the warp.
-// 1/d for a positive normal FP64 d by Newton's method for the reciprocal,
-// r <- r + r (1 - d r), from the hardware's approximate reciprocal
-// (rcp.approx.ftz.f64); each step doubles the correct bits, two reach FP64
-// rounding.  Five FP64 operations against about twice that for a division.
-__device__ __forceinline__ double recip_newton(double d)
-{
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
-}
 
 __global__ void __launch_bounds__(64) gram_spike_kernel(ProjectPlan p, const int* __restrict__ order)
 {

@@ -90,9 +90,13 @@ __global__ void __launch_bounds__(kBuildThreads) table_round_kernel(
     for (int i = 1 + threadIdx.x; i <= N; i += blockDim.x) {
         const double h = (double)xk[i] - (double)xk[i - 1];
         if (!(h > 0.0)) st |= 1;
-        const double s = ((double)vk[i] - (double)vk[i - 1]) / h;
+        // one Newton-refined reciprocal instead of two FP64 divisions (this
+        // single-CTA kernel runs on one SM's FP64 pipe); h <= 0, flagged
+        // above, keeps the division's inf and NaN
+        const double r = h > 0.0 ? recip_newton(h) : 1.0 / h;
+        const double s = ((double)vk[i] - (double)vk[i - 1]) * r;
         const float fs = __double2float_rn(s);
-        const float fr = __double2float_rn(1.0 / h);
+        const float fr = __double2float_rn(r);
         if (!isfinite(fs) || !isfinite(fr)) st |= 4;
         slope[i] = fs;
         inv_h[i] = fr;
